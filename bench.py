@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Benchmark: multi-depth ray casting + sensor model at 4096 envs x 2 cameras x 64x48 px.
+
+One step = one call of the C ABI's rpl_render (per-env link/camera transforms, then the fused
+ray-cast + sensor kernel) over all envs with the next pose set; inputs are resident in HBM.
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead on a bounded
+sample of the same workload.
+
+Multi-GPU (torchrun): each rank renders its own 4096 envs (env_offset = rank * 4096), no data-path
+collective; the barrier and the max-over-ranks time only bracket the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Grays/s and depth frames/s at 4096 envs; serve p50/p99 latency vs plain FP32"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "render_kernel_traffic.json")
+NODE_BYTES, TRI_BYTES, BOX_BYTES = 64, 48, 32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--envs", type=int, default=4096)
+    ap.add_argument("--tiles", type=int, default=20)
+    ap.add_argument("--pose-sets", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(args, rank):
+    from paper_2602_03002_gb300 import workloads as W
+    return W.config_scale(n_steps=args.pose_sets, n_envs=args.envs, tiles=args.tiles, seed=rank)
+
+
+def workload_name(w):
+    return ("plain FP32 at scale: %d envs x %d cams x %dx%d px; terrain %d tris (%dx%d tiles of 8x8 m at "
+            "0.05 m: stairs 0.22/0.25/0.30 m run, 20 deg slopes, stepping stones); %d links x %d-tri meshes; "
+            "sensor sigma %.2f m, %.0f%% dropout, latency 0-%d steps"
+            % (w.n_envs, len(w.cameras), w.cameras[0].width, w.cameras[0].height, len(w.terrain_tris),
+               int(round(np.sqrt(len(w.terrain_tris) / 51200))), int(round(np.sqrt(len(w.terrain_tris) / 51200))),
+               w.n_links, len(w.link_tris[0]), w.sensor.sigma_abs, 100 * w.sensor.p_drop, w.sensor.max_latency))
+
+
+def peaks():
+    try:
+        with open(PEAKS) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("render.cu", "render.h", "bvh.h"):
+        with open(os.path.join(ROOT, "paper_2602_03002_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(rays):
+    """DRAM bytes per launch from the committed ncu capture, scaled by rays; None if the kernel changed."""
+    try:
+        with open(TRAFFIC) as f:
+            t = json.load(f)
+        if t.get("kernel_sha") != kernel_hash():
+            return None
+        return float(t["dram_bytes"]) * rays / float(t["rays"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (SM clock, throttle reasons)."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(w, seconds, rank):
+    """The FP64 oracle, as it stands, on a bounded sample of rays of the same workload."""
+    import oracle
+    cores = os.cpu_count() or 1
+    sc = oracle.OracleScene.from_workload(w)
+    rng = np.random.default_rng(1234)
+
+    def sample(n):
+        e = rng.integers(0, w.n_envs, n)
+        c = rng.integers(0, len(w.cameras), n)
+        x = rng.integers(0, w.cameras[0].width, n)
+        y = rng.integers(0, w.cameras[0].height, n)
+        return np.stack([e, c, x, y], 1)
+
+    t = time.perf_counter()
+    sc.render(w.cameras, w.poses, 0, sample(cores), w.sensor, flags=False, threads=cores)
+    probe = time.perf_counter() - t
+    n = max(cores, int(cores * seconds / max(probe, 1e-3)))
+    rays = sample(n)
+    t = time.perf_counter()
+    sc.render(w.cameras, w.poses, 0, rays, w.sensor, flags=False, threads=cores)
+    dt = time.perf_counter() - t
+    sc.close()
+    return n, dt, cores
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    w = workload(args, 0)
+    vals = []
+    n_tot = dt_tot = 0
+    for k in range(args.warmup + args.steps):
+        n, dt, cores = cpu_baseline(w, max(1.0, args.cpu_seconds / max(1, args.steps)), 0)
+        if k >= args.warmup:
+            vals.append(n / dt)
+            n_tot += n
+            dt_tot += dt
+    rate = n_tot / dt_tot
+    sample = "%d rays per step drawn uniformly over (env, camera, pixel), brute force over all %d triangles" % (
+        n_tot // max(1, args.steps), len(w.terrain_tris) + sum(len(t) for t in w.link_tris))
+    line = {"impl": "reference", "metric": METRIC, "value": rate / 1e9, "unit": "Grays/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt_tot / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(w)},
+            "frames_per_s": rate / w.cameras[0].width / w.cameras[0].height,
+            "e2e": {"value": rate / 1e9, "unit": "Grays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "cpu_baseline": {"value": rate / 1e9, "unit": "Grays/s", "cores": cores, "kind": "oracle",
+                             "sample": sample}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = local if torch.cuda.is_available() else 0
+    torch.cuda.set_device(dev)
+    from paper_2602_03002_gb300 import build as B, rpl
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    w = workload(args, rank)
+    env_offset = rank * args.envs
+    t0 = time.perf_counter()
+    scene = rpl.Scene.from_workload(w, device=dev)
+    build_s = time.perf_counter() - t0
+    view = rpl.View.from_workload(scene, w)
+    info = scene.info()
+    stream = torch.cuda.Stream(dev)
+    poses = torch.from_numpy(w.poses).to(f"cuda:{dev}")
+    _, P = view.layout()
+    out = torch.empty((w.n_envs, P), dtype=torch.float32, device=f"cuda:{dev}")
+    rays = w.rays_per_step
+
+    # traversal counters (untimed): algorithmic fetch bytes per ray for the roofline
+    with torch.cuda.stream(stream):
+        cnt = view.render_counters(poses[0], 0, env_offset, out, stream)
+    b_nodes = (cnt["terrain_nodes"] + cnt["link_nodes"]) * NODE_BYTES
+    b_tris = (cnt["terrain_tris"] + cnt["link_tris"]) * TRI_BYTES
+    b_boxes = cnt["link_boxes"] * BOX_BYTES
+    # compulsory per-ray traffic: output store, ring write and (k > 0) ring read
+    b_io = rays * (4 + (8 if w.sensor.max_latency > 0 else 0))
+    alg_bytes = b_nodes + b_tris + b_boxes + b_io
+
+    view.reset(None, 0)
+    step = 0
+    S = poses.shape[0]
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            rpl.rpl_render(view.h, poses[step % S], step, env_offset, out, stream)
+            step += 1
+    stream.synchronize()
+    rpl.rpl_view_timing(view.h, True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        for _ in range(args.steps):
+            rpl.rpl_render(view.h, poses[step % S], step, env_offset, out, stream)
+            step += 1
+        end.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = start.elapsed_time(end)
+    kms = rpl.rpl_view_kernel_ms(view.h, min(args.steps, 256))
+    rpl.rpl_view_timing(view.h, False)
+    view.sync()
+    if world > 1:
+        t = torch.tensor([ms], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * rays / (ms_step / 1e3) / 1e9
+    frames = world * w.n_envs * len(w.cameras) / (ms_step / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned): H2D poses, render, D2H depth
+    e2e = None
+    if not args.no_e2e:
+        hp = [torch.from_numpy(w.poses[s]).pin_memory() for s in range(S)]
+        ho = torch.empty((w.n_envs, P), dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            rpl.rpl_render(view.h, hp[step % S], step, env_offset, ho, stream)
+            step += 1
+        if world > 1:
+            torch.distributed.barrier()
+        t = time.perf_counter()
+        n_e2e = max(3, args.steps // 2)
+        for _ in range(n_e2e):
+            rpl.rpl_render(view.h, hp[step % S], step, env_offset, ho, stream)
+            step += 1
+        e2e_s = (time.perf_counter() - t) / n_e2e
+        if world > 1:
+            tt = torch.tensor([e2e_s], device=f"cuda:{dev}")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": world * rays / e2e_s / 1e9, "unit": "Grays/s",
+               "h2d_bytes_per_step": int(hp[0].numel() * 4), "d2h_bytes_per_step": int(ho.numel() * 4),
+               "ms_per_step": 1e3 * e2e_s}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+    k_avg_s = statistics.mean(kms) / 1e3 if kms else ms_step / 1e3
+    peak, peak_src = peaks()
+    achieved = alg_bytes / k_avg_s / 1e9
+    traffic = traffic_per_launch(rays)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Grays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(w), "envs_per_gpu": w.n_envs, "cameras": len(w.cameras),
+                   "rays_per_step_per_gpu": rays, "pose_sets": S,
+                   "l2": "inputs larger than L2: terrain BVH %.2f GB resident, new poses each step"
+                         % (info["terrain_bytes"] / 1e9)},
+        "frames_per_s": frames,
+        "env_steps_per_s": world * w.n_envs / (ms_step / 1e3),
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "render_kernel", "kernel_ms": 1e3 * k_avg_s,
+                     "alg_bytes_per_ray": alg_bytes / rays, "peak_source": peak_src + " hbm_gbs",
+                     "per_ray": {"terrain_nodes": cnt["terrain_nodes"] / rays, "terrain_tris": cnt["terrain_tris"] / rays,
+                                 "link_boxes": cnt["link_boxes"] / rays, "link_nodes": cnt["link_nodes"] / rays,
+                                 "link_tris": cnt["link_tris"] / rays}},
+        "clocks": ck,
+        "e2e": e2e,
+        "scene": {"terrain_tris": info["terrain_tris"], "terrain_nodes": info["terrain_nodes"],
+                  "terrain_depth": info["terrain_depth"], "bvh_build_s": build_s},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        n, dt, cores = cpu_baseline(w, args.cpu_seconds, rank)
+        line["cpu_baseline"] = {"value": n / dt / 1e9, "unit": "Grays/s", "cores": cores, "kind": "oracle",
+                                "sample": "%d rays drawn uniformly over (env, camera, pixel) of step 0, FP64 "
+                                          "brute force over all triangles, %.1f s" % (n, dt)}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * rpl.h -- C ABI of the GB300 multi-depth ray-casting library (librpl.so).
+ *
+ * The library renders, for many simulated environments at once, the depth images of several
+ * cameras mounted on a robot by casting one ray per pixel against one shared static terrain
+ * triangle mesh and against that environment's own posed robot-link meshes, then applies a depth
+ * sensor model (latency ring buffer, additive noise, pixel dropout, range clipping).
+ * It follows Sec. 3.2.1 ("Efficient Multi-Depth System Simulation") and Algorithm 1 of
+ * "RPL: Learning Robust Humanoid Perceptive Locomotion on Challenging Terrains" (arXiv 2602.03002),
+ * and the perception rows of its domain-randomisation table (Appendix A.2).
+ *
+ * Conventions used by every call
+ *  - Status: every call returns rpl_status; nothing throws or aborts across the ABI.  The text of
+ *    the last failure on the calling thread is available from rpl_last_error().
+ *  - Pointers: arguments documented as "host or device" may point to host memory (pageable or
+ *    pinned) or to device memory of the scene's GPU; the library detects which.  Everything else
+ *    is host memory.
+ *  - Ownership: input arrays are copied or only read during the call; the caller keeps them.
+ *    Scenes and views own their device memory (BVHs, per-env transforms, ring buffers) and free
+ *    it in rpl_*_destroy.  Output buffers belong to the caller.
+ *  - Frames: link poses are float32 [E, L, 7] = (px, py, pz, qx, qy, qz, qw) in the world frame;
+ *    quaternions need not be normalised (they are normalised in FP32).  Camera mounts map the
+ *    OpenCV optical frame (x right, y down, z forward) into the mounting link's frame.
+ *  - Concurrency: a scene may be shared by many views and threads once its link meshes are added;
+ *    a view is used by one thread at a time.
+ */
+#ifndef RPL_H
+#define RPL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define RPL_API __attribute__((visibility("default")))
+#else
+#define RPL_API
+#endif
+
+typedef enum {
+    RPL_OK = 0,
+    RPL_ERR_INVALID_ARG = 1,    /* a null handle, bad size, index out of range, step out of order */
+    RPL_ERR_OUT_OF_MEMORY = 2,  /* host or device allocation failed */
+    RPL_ERR_CUDA = 3,           /* a CUDA runtime call or a kernel launch failed */
+    RPL_ERR_NOT_FOUND = 4,      /* no CUDA device with the requested ordinal */
+    RPL_ERR_CAPACITY = 5,       /* more cameras/links than the library supports, BVH too deep */
+    RPL_ERR_TIMEOUT = 6,        /* reserved for bounded device waits */
+    RPL_ERR_DEVICE_FAULT = 7    /* a kernel recorded an error (see rpl_last_error); sticky per view */
+} rpl_status;
+
+typedef struct rpl_scene *rpl_scene_t;   /* terrain + link BVHs, read-only once frozen */
+typedef struct rpl_view *rpl_view_t;     /* cameras, env count, sensor, per-env state */
+
+#define RPL_MAX_CAMERAS 8
+#define RPL_MAX_LINKS 64
+
+typedef enum { RPL_BVH2 = 0 } rpl_bvh_kind;
+typedef enum { RPL_DEPTH_Z = 0, RPL_DEPTH_RANGE = 1 } rpl_depth_kind;
+typedef enum { RPL_OUT_F32 = 0 } rpl_out_dtype;
+
+/* Scene options.  device: CUDA ordinal; bvh_kind: rpl_bvh_kind; max_leaf_size: triangles per BVH
+ * leaf (1..8, 0 = default 4); build_threads: host threads for the BVH build (0 = all cores). */
+typedef struct {
+    int32_t device;
+    int32_t bvh_kind;
+    int32_t max_leaf_size;
+    int32_t build_threads;
+} rpl_scene_opts;
+
+/* Pinhole camera.  Pixel (x, y), 0 <= x < width, 0 <= y < height, has the camera-frame ray
+ * r = ((x - cx)/fx, (y - cy)/fy, 1) (Sec. 3.2.1: r_c = K^-1 [x, y, 1]^T).  The camera pose is the
+ * pose of link `mount_link` composed with (offset_pos, offset_quat_xyzw).  Depths are clipped to
+ * [d_min, d_max]; a ray that hits nothing closer than d_max reports d_max (the far plane). */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    int32_t mount_link;
+    float offset_pos[3];
+    float offset_quat_xyzw[4];
+    float d_min, d_max;
+} rpl_camera;
+
+/* Depth-sensor model (Appendix A.2: process delay, noise, dropout).  For output step s, pixel p
+ * of camera c in global env g:
+ *   k  = (w0(g, c, 0xFFFFFFFF, s) * (max_latency + 1)) >> 32          latency in steps
+ *   s' = max(s - k, first step of the env since its reset)            source step
+ *   z  = raw depth of step s' (far plane d_max when nothing is hit)
+ *   if z < d_max: z += (sigma_abs + sigma_rel z) sqrt(-2 ln u1) cos(2 pi u2),
+ *                 u1 = (w1 + 1) 2^-32, u2 = w2 2^-32                     (Box-Muller)
+ *   z = min(max(z, d_min), d_max)
+ *   if w0 < floor(p_drop 2^32): z = fill                               dropout
+ * where (w0, w1, w2, w3) = Philox4x32-10(counter = (g, c, p, s' mod 2^32),
+ * key = (seed[0] ^ (s' >> 32), seed[1])) for the noise and dropout words, and likewise with s for
+ * the latency word.  All zeros (the default) turns the model off except for the clip. */
+typedef struct {
+    float sigma_abs, sigma_rel, p_drop, fill;
+    int32_t max_latency;          /* 0..15 */
+    uint32_t seed[2];
+    int32_t depth_kind;           /* rpl_depth_kind: z-depth along the optical axis (default) or range */
+    int32_t out_dtype;            /* rpl_out_dtype */
+} rpl_sensor_params;
+
+/* Statistics of a built scene (sizes in bytes on the device). */
+typedef struct {
+    int64_t terrain_tris, terrain_nodes, terrain_bytes;
+    int32_t terrain_depth, n_links;
+    int64_t link_tris, link_nodes, link_bytes;
+    int32_t link_depth, frozen;
+} rpl_scene_info;
+
+/* Traversal counters of one render (see rpl_render_counters). */
+typedef struct {
+    uint64_t rays;
+    uint64_t terrain_nodes, terrain_tris;   /* BVH nodes fetched, triangles tested */
+    uint64_t link_boxes, link_nodes, link_tris;
+} rpl_counters;
+
+/* ---------------------------------------------------------------------------------------------
+ * Scene
+ * ------------------------------------------------------------------------------------------- */
+
+/* Build the BVH of the static terrain (world frame) once and upload it (Sec. 3.2.1: the terrain is
+ * one shared static mesh).  verts: [n_verts, 3] float32, tris: [n_tris, 3] int32 vertex indices,
+ * both host or device.  n_tris may be 0 (nothing but links is hit).  opts may be NULL.
+ * Errors: INVALID_ARG (index out of range, negative size), NOT_FOUND, OUT_OF_MEMORY, CUDA. */
+RPL_API rpl_status rpl_scene_create(const float *verts, int64_t n_verts, const int32_t *tris,
+                                    int64_t n_tris, const rpl_scene_opts *opts, rpl_scene_t *out);
+
+/* Add the mesh of link `link_id` (0 <= link_id < RPL_MAX_LINKS) in its own frame and build its BVH
+ * once (Sec. 3.2.1: body meshes stay canonical in their local frames, rays are moved instead, so
+ * nothing is refitted per frame).  Links without a mesh are never hit.  verts/tris as in
+ * rpl_scene_create, host or device.  Must come before the first rpl_view_create on the scene,
+ * which freezes it (INVALID_ARG afterwards). */
+RPL_API rpl_status rpl_link_mesh_add(rpl_scene_t scene, int32_t link_id, const float *verts,
+                                     int64_t n_verts, const int32_t *tris, int64_t n_tris);
+
+RPL_API rpl_status rpl_scene_info_get(rpl_scene_t scene, rpl_scene_info *info);
+
+/* Host-only BVH build with the same builder the scene uses (no GPU needed), for inspection and tests.
+ * Writes the nodes (64-byte records: child-0 box x lo/hi, y lo/hi; child-1 box x lo/hi, y lo/hi;
+ * child-0 z lo/hi, child-1 z lo/hi; int32 child0, child1, count0, count1 -- a child >= 0 is an inner
+ * node, < 0 a leaf whose first triangle is ~child) and the leaf-ordered triangles (48-byte records:
+ * v0 xyz + original index as int32 bits, v1 xyz + 0, v2 xyz + 0).  Call with nodes_out = NULL to
+ * learn *n_nodes first; tris_out must hold n_tris records or be NULL.  Errors: INVALID_ARG,
+ * CAPACITY (nodes_cap too small), OUT_OF_MEMORY. */
+RPL_API rpl_status rpl_bvh_build_host(const float *verts, int64_t n_verts, const int32_t *tris,
+                                      int64_t n_tris, int32_t max_leaf, int32_t threads, void *nodes_out,
+                                      int64_t nodes_cap, void *tris_out, int64_t *n_nodes, int32_t *depth);
+
+/* Frees the scene's device memory.  Views of the scene must be destroyed first. */
+RPL_API void rpl_scene_destroy(rpl_scene_t scene);
+
+/* ---------------------------------------------------------------------------------------------
+ * View: one trainer's environments
+ * ------------------------------------------------------------------------------------------- */
+
+/* A view of n_envs environments with n_links links each (poses are [n_envs, n_links, 7]).
+ * Freezes the scene.  n_envs may be 0.  Errors: INVALID_ARG, CAPACITY (n_links > RPL_MAX_LINKS),
+ * OUT_OF_MEMORY, CUDA. */
+RPL_API rpl_status rpl_view_create(rpl_scene_t scene, int32_t n_envs, int32_t n_links, rpl_view_t *out);
+
+/* Set the cameras (1..RPL_MAX_CAMERAS; they may differ in size).  per_env_intrinsics, host or
+ * device, is NULL or [n_envs, n_cams, 4] float32 (fx, fy, cx, cy) overriding each camera's
+ * intrinsics per env (Sec. 3.2.1: batched inverse intrinsics for per-env FOV randomisation).
+ * Restarts the sensor state (as rpl_view_reset with no mask).  Errors: INVALID_ARG (size <= 0,
+ * fx or fy == 0, mount_link out of range, d_min > d_max), CAPACITY, OUT_OF_MEMORY. */
+RPL_API rpl_status rpl_cameras_set(rpl_view_t view, const rpl_camera *cams, int32_t n_cams,
+                                   const float *per_env_intrinsics);
+
+/* Set the sensor model (see rpl_sensor_params).  Allocates the latency ring buffer,
+ * [n_envs, max_latency + 1, pixels per env] float32, and restarts the sensor state.
+ * Errors: INVALID_ARG (max_latency outside 0..15, p_drop outside [0, 1], negative sigma),
+ * OUT_OF_MEMORY. */
+RPL_API rpl_status rpl_sensor_set(rpl_view_t view, const rpl_sensor_params *params);
+
+/* Layout of one render's output: env-major, cameras packed per env, row-major pixels; camera c
+ * of env e starts at e * total_per_env + cam_offsets[c].  cam_offsets has room for n_cams + 1
+ * entries (the last one is total_per_env); either pointer may be NULL. */
+RPL_API rpl_status rpl_view_layout(rpl_view_t view, int64_t *cam_offsets, int64_t *total_per_env);
+
+/* Render step `step` (Algorithm 1 plus the sensor model).
+ *   link_poses  host or device, [n_envs, n_links, 7] float32 (see conventions)
+ *   step        render-step counter: the first call after rpl_view_create / rpl_cameras_set /
+ *               rpl_sensor_set / a full rpl_view_reset may use any value; afterwards each call
+ *               uses the previous step (re-render) or the previous step + 1 (INVALID_ARG else)
+ *   env_offset  global id of env 0 of this view (keys the random streams, so that a range of envs
+ *               rendered by another GPU or process draws the same numbers); env_offset + n_envs
+ *               must not exceed 2^32
+ *   depth_out   host or device, n_envs * total_per_env float32 (see rpl_view_layout)
+ *   stream      cudaStream_t to run on (NULL = the legacy default stream)
+ * With device buffers the call only enqueues work and returns; it does not allocate or
+ * synchronise, so it can be captured into a CUDA graph (a captured graph replays the step it was
+ * captured with).  With a host buffer the poses are staged through view-owned device memory
+ * (allocated on the first such call) and the call returns after the depth is in depth_out.
+ * Errors: INVALID_ARG, CUDA, DEVICE_FAULT (an earlier launch on this view recorded a kernel
+ * error; call rpl_sync to read it and clear it). */
+RPL_API rpl_status rpl_render(rpl_view_t view, const float *link_poses, int64_t step,
+                              int64_t env_offset, void *depth_out, void *stream);
+
+/* Restart the sensor history at `step` for the envs whose byte in env_mask (host or device,
+ * [n_envs] uint8) is non-zero, or for all envs when env_mask is NULL: from then on the source step
+ * of those envs is never older than `step`.  With a mask, `step` must be the next step to render
+ * (last rendered step + 1); with no mask the next render must use `step`.  Asynchronous on
+ * `stream`.  Errors: INVALID_ARG, CUDA. */
+RPL_API rpl_status rpl_view_reset(rpl_view_t view, const uint8_t *env_mask, int64_t step, void *stream);
+
+/* Wait for the view's work on its last stream, then report and clear a recorded kernel error
+ * (DEVICE_FAULT), or a CUDA error. */
+RPL_API rpl_status rpl_sync(rpl_view_t view);
+
+/* Render like rpl_render (device buffers only) with the counting kernel variant, synchronise, and
+ * return how many BVH nodes and triangles the traversal touched.  Does not advance the sensor
+ * state check (it re-renders `step`).  For measurement only. */
+RPL_API rpl_status rpl_render_counters(rpl_view_t view, const float *link_poses, int64_t step,
+                                       int64_t env_offset, void *depth_out, void *stream,
+                                       rpl_counters *counters);
+
+/* Measurement aid: when enabled, each following render records a CUDA event pair on its stream
+ * around the traversal kernel (a ring of the last 256 launches).  rpl_view_kernel_ms waits for and
+ * returns the durations in milliseconds of the last min(max_n, recorded) launches, oldest first. */
+RPL_API rpl_status rpl_view_timing(rpl_view_t view, int32_t enable);
+RPL_API rpl_status rpl_view_kernel_ms(rpl_view_t view, float *ms, int32_t max_n, int32_t *n_out);
+
+RPL_API void rpl_view_destroy(rpl_view_t view);
+
+/* Message of the last failed call on this thread ("" if none). */
+RPL_API const char *rpl_last_error(void);
+
+/* Library version, for the Python binding's compatibility check. */
+RPL_API int32_t rpl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPL_H */

@@ -1,0 +1,411 @@
+// render.cu -- sm_103a kernels of the multi-depth ray-casting path (Sec. 3.2.1, Algorithm 1) and of
+// the depth-sensor model (Appendix A.2).
+//
+//   prep_kernel    one thread per (env, link): normalised link rotation, world->link transform and
+//                  the link's world AABB; one thread per (env, camera): camera pose = link pose
+//                  composed with the mount offset.
+//   render_kernel  one thread per pixel ray, one warp per 8x4 pixel tile of one (env, camera):
+//                  BuildDepthRay -> links whose world AABB the ray meets within the running bound
+//                  (ray moved into the link frame, link BVH traversed, bound shrinks on each hit)
+//                  -> terrain BVH traversal with the bound -> far-plane clip -> fused sensor model
+//                  (ring-buffer write, latency select, noise, clip, dropout) -> store.
+//
+// The path is pointer chasing, not a dense contraction, so it runs on the SIMT pipes: node and
+// triangle fetches are 16-byte read-only vector loads, the per-ray stack is short, rays of a warp
+// are a compact pixel tile so their fetches coalesce and hit the same cache lines.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "render.h"
+
+namespace rpl {
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+//   (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
+// the key advanced by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 sensor_words(uint32_t env, uint32_t cam, uint32_t pix, int64_t step,
+                                              uint32_t seed0, uint32_t seed1) {
+    const uint64_t s = (uint64_t)step;
+    return philox10(make_uint4(env, cam, pix, (uint32_t)s), seed0 ^ (uint32_t)(s >> 32), seed1);
+}
+
+// Rotation matrix (row-major) of a quaternion (x, y, z, w), normalised in FP32.
+__device__ __forceinline__ void quat_rot(float x, float y, float z, float w, float R[9]) {
+    const float inv = 1.0f / sqrtf(x * x + y * y + z * z + w * w);
+    x *= inv; y *= inv; z *= inv; w *= inv;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - z * w);       R[2] = 2.f * (x * z + y * w);
+    R[3] = 2.f * (x * y + z * w);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - x * w);
+    R[6] = 2.f * (x * z - y * w);       R[7] = 2.f * (y * z + x * w);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+__device__ __forceinline__ float pad_lo(float v) { return v - (fabsf(v) * 0x1p-18f + 1e-5f); }
+__device__ __forceinline__ float pad_hi(float v) { return v + (fabsf(v) * 0x1p-18f + 1e-5f); }
+
+__global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepParams p) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n_link = (int64_t)p.E * p.L;
+    if (i < n_link) {
+        const int l = (int)(i % p.L);
+        const float *q = p.poses + 7 * i;
+        float R[9];
+        quat_rot(q[3], q[4], q[5], q[6], R);
+        const float tx = q[0], ty = q[1], tz = q[2];
+        p.link_xf[3 * i + 0] = make_float4(R[0], R[3], R[6], tx);
+        p.link_xf[3 * i + 1] = make_float4(R[1], R[4], R[7], ty);
+        p.link_xf[3 * i + 2] = make_float4(R[2], R[5], R[8], tz);
+        const float4 lo = p.link_root[2 * l], hi = p.link_root[2 * l + 1];
+        if (!(lo.x <= hi.x)) {
+            p.link_box[2 * i + 0] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+            p.link_box[2 * i + 1] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+            return;
+        }
+        const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y), cz = 0.5f * (lo.z + hi.z);
+        const float hx = 0.5f * (hi.x - lo.x), hy = 0.5f * (hi.y - lo.y), hz = 0.5f * (hi.z - lo.z);
+        const float wx = R[0] * cx + R[1] * cy + R[2] * cz + tx;
+        const float wy = R[3] * cx + R[4] * cy + R[5] * cz + ty;
+        const float wz = R[6] * cx + R[7] * cy + R[8] * cz + tz;
+        // slack covers the rounding of the centre/extent arithmetic above
+        const float ex = fabsf(R[0]) * hx + fabsf(R[1]) * hy + fabsf(R[2]) * hz + 1e-6f;
+        const float ey = fabsf(R[3]) * hx + fabsf(R[4]) * hy + fabsf(R[5]) * hz + 1e-6f;
+        const float ez = fabsf(R[6]) * hx + fabsf(R[7]) * hy + fabsf(R[8]) * hz + 1e-6f;
+        p.link_box[2 * i + 0] = make_float4(pad_lo(wx - ex), pad_lo(wy - ey), pad_lo(wz - ez), 0.f);
+        p.link_box[2 * i + 1] = make_float4(pad_hi(wx + ex), pad_hi(wy + ey), pad_hi(wz + ez), 0.f);
+        return;
+    }
+    const int64_t j = i - n_link;
+    if (j >= (int64_t)p.E * p.C) return;
+    const int e = (int)(j / p.C), c = (int)(j % p.C);
+    const CamDev &cam = p.cams[c];
+    const float *q = p.poses + 7 * ((int64_t)e * p.L + cam.mount);
+    float Rl[9], Ro[9];
+    quat_rot(q[3], q[4], q[5], q[6], Rl);
+    quat_rot(cam.off_quat[0], cam.off_quat[1], cam.off_quat[2], cam.off_quat[3], Ro);
+    float Rc[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            Rc[3 * r + k] = Rl[3 * r + 0] * Ro[k] + Rl[3 * r + 1] * Ro[3 + k] + Rl[3 * r + 2] * Ro[6 + k];
+    const float ox = Rl[0] * cam.off_pos[0] + Rl[1] * cam.off_pos[1] + Rl[2] * cam.off_pos[2];
+    const float oy = Rl[3] * cam.off_pos[0] + Rl[4] * cam.off_pos[1] + Rl[5] * cam.off_pos[2];
+    const float oz = Rl[6] * cam.off_pos[0] + Rl[7] * cam.off_pos[1] + Rl[8] * cam.off_pos[2];
+    p.cam_xf[4 * j + 0] = make_float4(Rc[0], Rc[1], Rc[2], q[0]);
+    p.cam_xf[4 * j + 1] = make_float4(Rc[3], Rc[4], Rc[5], q[1]);
+    p.cam_xf[4 * j + 2] = make_float4(Rc[6], Rc[7], Rc[8], q[2]);
+    p.cam_xf[4 * j + 3] = make_float4(ox, oy, oz, 0.f);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Ray state for one mesh query.  Box tests use the rounded origin `o` with 1/d; the triangle test
+// uses the origin as base + off (both FP32), so vertex - origin keeps the precision of the small
+// difference even 80 m away from the world origin.
+// ---------------------------------------------------------------------------------------------
+struct Ray {
+    float3 invd, oinv;    // 1/d and o/d for the slab test
+    float3 base, off;     // triangle-test origin = base + off
+    float Sx, Sy, Sz;     // watertight shear constants
+    int kz;               // dominant axis of d
+};
+
+__device__ __forceinline__ float safe_rcp(float v) {
+    return 1.0f / (fabsf(v) > 1e-20f ? v : copysignf(1e-20f, v));
+}
+
+__device__ __forceinline__ float comp(const float3 &v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+__device__ __forceinline__ void make_ray(Ray &r, float3 base, float3 off, float3 d) {
+    const float3 o = make_float3(base.x + off.x, base.y + off.y, base.z + off.z);
+    r.invd = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    r.oinv = make_float3(o.x * r.invd.x, o.y * r.invd.y, o.z * r.invd.z);
+    r.base = base;
+    r.off = off;
+    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    r.kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    const int kx = r.kz == 2 ? 0 : r.kz + 1;
+    const int ky = kx == 2 ? 0 : kx + 1;
+    const float dz = comp(d, r.kz);
+    r.Sx = comp(d, kx) / dz;
+    r.Sy = comp(d, ky) / dz;
+    r.Sz = 1.0f / dz;
+}
+
+// Slab test of one child box against (0, tmax]; returns the entry distance or +inf.
+__device__ __forceinline__ float slab(const Ray &r, float lox, float hix, float loy, float hiy, float loz,
+                                      float hiz, float tmax) {
+    const float x0 = fmaf(lox, r.invd.x, -r.oinv.x), x1 = fmaf(hix, r.invd.x, -r.oinv.x);
+    const float y0 = fmaf(loy, r.invd.y, -r.oinv.y), y1 = fmaf(hiy, r.invd.y, -r.oinv.y);
+    const float z0 = fmaf(loz, r.invd.z, -r.oinv.z), z1 = fmaf(hiz, r.invd.z, -r.oinv.z);
+    const float tin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
+    const float tout = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
+    return tin <= tout ? tin : CUDART_INF_F;
+}
+
+// Vertex relative to the ray origin, permuted so the dominant axis comes last, then sheared so that
+// the ray becomes the +z axis (Woop, Benthin, Wald 2013, "Watertight Ray/Triangle Intersection").
+template <bool kSplit>
+__device__ __forceinline__ float3 shear_vertex(const Ray &r, float vx, float vy, float vz) {
+    float ax = vx - r.base.x, ay = vy - r.base.y, az = vz - r.base.z;
+    if (kSplit) {
+        ax -= r.off.x;
+        ay -= r.off.y;
+        az -= r.off.z;
+    }
+    const float3 a = make_float3(ax, ay, az);
+    const int kx = r.kz == 2 ? 0 : r.kz + 1;
+    const int ky = kx == 2 ? 0 : kx + 1;
+    const float pz = comp(a, r.kz);
+    return make_float3(fmaf(-r.Sx, pz, comp(a, kx)), fmaf(-r.Sy, pz, comp(a, ky)), r.Sz * pz);
+}
+
+// Two-sided, closed watertight test.  The 2D edge functions are evaluated without contraction, so a
+// shared edge yields exactly negated values in its two triangles and no ray slips between them.
+template <bool kSplit>
+__device__ __forceinline__ bool tri_hit(const Ray &r, const float4 &v0, const float4 &v1, const float4 &v2,
+                                        float &tmax) {
+    const float3 A = shear_vertex<kSplit>(r, v0.x, v0.y, v0.z);
+    const float3 B = shear_vertex<kSplit>(r, v1.x, v1.y, v1.z);
+    const float3 C = shear_vertex<kSplit>(r, v2.x, v2.y, v2.z);
+    const float U = __fsub_rn(__fmul_rn(C.x, B.y), __fmul_rn(C.y, B.x));
+    const float V = __fsub_rn(__fmul_rn(A.x, C.y), __fmul_rn(A.y, C.x));
+    const float W = __fsub_rn(__fmul_rn(B.x, A.y), __fmul_rn(B.y, A.x));
+    const bool has_neg = (U < 0.f) || (V < 0.f) || (W < 0.f);
+    const bool has_pos = (U > 0.f) || (V > 0.f) || (W > 0.f);
+    if (has_neg && has_pos) return false;
+    const float det = U + V + W;
+    if (det == 0.f) return false;
+    const float T = U * A.z + V * B.z + W * C.z;
+    if (det > 0.f ? (T <= 0.f || T > tmax * det) : (T >= 0.f || T < tmax * det)) return false;
+    const float t = __fdiv_rn(T, det);
+    if (!(t > 0.f && t < tmax)) return false;
+    tmax = t;
+    return true;
+}
+
+struct Counts {
+    uint32_t nodes = 0, tris = 0;
+};
+
+template <bool kSplit, bool kCount>
+__device__ __forceinline__ void leaf(const float4 *__restrict__ tris, int first, int count, const Ray &r,
+                                     float &tmax, bool &hit, Counts &cnt) {
+#pragma unroll 1
+    for (int i = first; i < first + count; ++i) {
+        const float4 a = __ldg(tris + 3 * i), b = __ldg(tris + 3 * i + 1), c = __ldg(tris + 3 * i + 2);
+        if (kCount) ++cnt.tris;
+        hit |= tri_hit<kSplit>(r, a, b, c, tmax);
+    }
+}
+
+// Closest hit below tmax in one BVH; tmax shrinks to the hit distance.  Returns false when the stack
+// would overflow (never for scenes accepted at build time).
+template <bool kSplit, bool kCount>
+__device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const float4 *__restrict__ tris, int root,
+                                         const Ray &r, float &tmax, bool &hit, Counts &cnt) {
+    int stack_node[kStackDepth];
+    float stack_t[kStackDepth];
+    int sp = 0;
+    int cur = root;
+#pragma unroll 1
+    for (;;) {
+        const float4 *n = nodes + 4 * cur;
+        const float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2);
+        const int4 n3 = __ldg(reinterpret_cast<const int4 *>(n + 3));
+        if (kCount) ++cnt.nodes;
+        float t0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmax);
+        float t1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmax);
+        if (t0 != CUDART_INF_F && n3.x < 0) {
+            leaf<kSplit, kCount>(tris, ~n3.x, n3.z, r, tmax, hit, cnt);
+            t0 = CUDART_INF_F;
+            if (t1 > tmax) t1 = CUDART_INF_F;
+        }
+        if (t1 != CUDART_INF_F && n3.y < 0) {
+            leaf<kSplit, kCount>(tris, ~n3.y, n3.w, r, tmax, hit, cnt);
+            t1 = CUDART_INF_F;
+            if (t0 > tmax) t0 = CUDART_INF_F;
+        }
+        const bool h0 = t0 != CUDART_INF_F, h1 = t1 != CUDART_INF_F;
+        if (h0 && h1) {
+            const bool first0 = t0 <= t1;
+            if (sp == kStackDepth) return false;
+            stack_node[sp] = first0 ? n3.y : n3.x;
+            stack_t[sp] = first0 ? t1 : t0;
+            ++sp;
+            cur = first0 ? n3.x : n3.y;
+            continue;
+        }
+        if (h0) { cur = n3.x; continue; }
+        if (h1) { cur = n3.y; continue; }
+        // pop the nearest pending subtree that still starts before the bound
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (stack_t[sp] <= tmax) {
+                cur = stack_node[sp];
+                found = true;
+                break;
+            }
+        }
+        if (!found) return true;
+    }
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(128) render_kernel(const __grid_constant__ RenderParams p) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (warp >= (int64_t)p.E * p.tiles_per_env) return;
+    const int e = (int)(warp / p.tiles_per_env);
+    const int r_tile = (int)(warp - (int64_t)e * p.tiles_per_env);
+    int c = 0;
+    while (c + 1 < p.C && r_tile >= p.cams[c + 1].tile_off) ++c;
+    const CamDev &cam = p.cams[c];
+    const int t = r_tile - cam.tile_off;
+    const int x = (t % cam.tiles_x) * 8 + (lane & 7);
+    const int y = (t / cam.tiles_x) * 4 + (lane >> 3);
+    if (x >= cam.width || y >= cam.height) return;
+
+    // BuildDepthRay: r = K^-1 [x, y, 1], d = R_c r / |r|, m = 1 / |r|
+    float fx = cam.fx, fy = cam.fy, cx = cam.cx, cy = cam.cy;
+    if (p.intr) {
+        const float4 k = __ldg(reinterpret_cast<const float4 *>(p.intr) + (int64_t)e * p.C + c);
+        fx = k.x; fy = k.y; cx = k.z; cy = k.w;
+    }
+    const float4 *cx4 = p.cam_xf + 4 * ((int64_t)e * p.C + c);
+    const float4 R0 = __ldg(cx4), R1 = __ldg(cx4 + 1), R2 = __ldg(cx4 + 2), OF = __ldg(cx4 + 3);
+    const float rx = __fdiv_rn((float)x - cx, fx), ry = __fdiv_rn((float)y - cy, fy);
+    const float inv_n = 1.0f / sqrtf(rx * rx + ry * ry + 1.0f);
+    const float ux = rx * inv_n, uy = ry * inv_n, uz = inv_n;
+    const float3 d = make_float3(R0.x * ux + R0.y * uy + R0.z * uz, R1.x * ux + R1.y * uy + R1.z * uz,
+                                 R2.x * ux + R2.y * uy + R2.z * uz);
+    const float3 base = make_float3(R0.w, R1.w, R2.w);
+    const float3 off = make_float3(OF.x, OF.y, OF.z);
+    const float m = p.depth_kind == RPL_DEPTH_Z ? inv_n : 1.0f;
+    float tmax = __fdiv_rn(cam.d_max, m);
+    bool hit = false;
+    bool ok = true;
+    Counts cnt_t, cnt_l;
+    uint32_t n_boxes = 0;
+
+    Ray ray;
+    make_ray(ray, base, off, d);
+
+    // 1) dynamic robot bodies: rays move into each link frame (o_b = R^T (o - t), d_b = R^T d)
+#pragma unroll 1
+    for (int l = 0; l < p.L; ++l) {
+        const int root = p.lroot[l];
+        if (root < 0) continue;
+        const int64_t el = (int64_t)e * p.L + l;
+        const float4 blo = __ldg(p.link_box + 2 * el), bhi = __ldg(p.link_box + 2 * el + 1);
+        if (kCount) ++n_boxes;
+        if (slab(ray, blo.x, bhi.x, blo.y, bhi.y, blo.z, bhi.z, tmax) == CUDART_INF_F) continue;
+        const float4 X0 = __ldg(p.link_xf + 3 * el), X1 = __ldg(p.link_xf + 3 * el + 1),
+                     X2 = __ldg(p.link_xf + 3 * el + 2);
+        const float3 rel = make_float3((base.x - X0.w) + off.x, (base.y - X1.w) + off.y, (base.z - X2.w) + off.z);
+        const float3 ob = make_float3(X0.x * rel.x + X0.y * rel.y + X0.z * rel.z,
+                                      X1.x * rel.x + X1.y * rel.y + X1.z * rel.z,
+                                      X2.x * rel.x + X2.y * rel.y + X2.z * rel.z);
+        const float3 db = make_float3(X0.x * d.x + X0.y * d.y + X0.z * d.z, X1.x * d.x + X1.y * d.y + X1.z * d.z,
+                                      X2.x * d.x + X2.y * d.y + X2.z * d.z);
+        Ray lr;
+        make_ray(lr, ob, make_float3(0.f, 0.f, 0.f), db);
+        ok &= traverse<false, kCount>(p.lnodes, p.ltris, root, lr, tmax, hit, cnt_l);
+    }
+    // 2) static terrain, bounded by the closest body hit
+    ok &= traverse<true, kCount>(p.tnodes, p.ttris, 0, ray, tmax, hit, cnt_t);
+    if (!ok) atomicOr(p.err, 1);
+
+    float z = hit ? fminf(m * tmax, cam.d_max) : cam.d_max;
+    const uint32_t pix = (uint32_t)(y * cam.width + x);
+    const int64_t col = (int64_t)cam.pix_off + pix;
+    if (p.sensor_on) {
+        const int64_t step = p.step;
+        const int64_t span = p.span;
+        const uint32_t ge = p.env_offset + (uint32_t)e;
+        int64_t src = step;
+        if (span > 1) {
+            const int64_t slot = ((step % span) + span) % span;
+            p.ring[((int64_t)e * span + slot) * p.pix_per_env + col] = z;
+            const uint4 wl = sensor_words(ge, (uint32_t)c, 0xFFFFFFFFu, step, p.seed0, p.seed1);
+            const int64_t k = (int64_t)__umulhi(wl.x, (uint32_t)span);
+            src = step - k;
+            const int64_t first = __ldg(p.s_first + e);
+            if (src < first) src = first;
+            if (src != step) {
+                const int64_t sslot = ((src % span) + span) % span;
+                z = p.ring[((int64_t)e * span + sslot) * p.pix_per_env + col];
+            }
+        }
+        const uint4 w = sensor_words(ge, (uint32_t)c, pix, src, p.seed0, p.seed1);
+        if (z < cam.d_max) {
+            const float u1 = ((float)w.y + 1.0f) * 0x1p-32f;
+            const float u2 = (float)w.z * 0x1p-32f;
+            const float n = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+            z = z + (p.sigma_abs + p.sigma_rel * z) * n;
+        }
+        z = fminf(fmaxf(z, cam.d_min), cam.d_max);
+        if ((uint64_t)w.x < p.drop_thr) z = p.fill;
+    } else {
+        z = fminf(fmaxf(z, cam.d_min), cam.d_max);
+    }
+    p.out[(int64_t)e * p.pix_per_env + col] = z;
+
+    if (kCount) {
+        const unsigned mask = __activemask();
+        const unsigned v[6] = {1u, cnt_t.nodes, cnt_t.tris, n_boxes, cnt_l.nodes, cnt_l.tris};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const unsigned s = __reduce_add_sync(mask, v[k]);
+            if (lane == __ffs(mask) - 1) atomicAdd(p.counters + k, (unsigned long long)s);
+        }
+    }
+}
+
+__global__ void set_first_kernel(int64_t *s_first, int32_t E, int64_t step, const uint8_t *mask) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < E && (mask == nullptr || mask[i] != 0)) s_first[i] = step;
+}
+
+}  // namespace
+
+cudaError_t launch_prep(const PrepParams &p, cudaStream_t s) {
+    const int64_t n = (int64_t)p.E * (p.L + p.C);
+    if (n == 0) return cudaSuccess;
+    prep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
+    const int64_t warps = (int64_t)p.E * p.tiles_per_env;
+    if (warps == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((warps + 3) / 4);
+    if (count)
+        render_kernel<true><<<blocks, 128, 0, s>>>(p);
+    else
+        render_kernel<false><<<blocks, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_first(int64_t *s_first, int32_t E, int64_t step, const uint8_t *mask, cudaStream_t s) {
+    if (E == 0) return cudaSuccess;
+    set_first_kernel<<<(E + 255) / 256, 256, 0, s>>>(s_first, E, step, mask);
+    return cudaGetLastError();
+}
+
+}  // namespace rpl

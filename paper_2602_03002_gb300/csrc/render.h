@@ -1,0 +1,69 @@
+// render.h -- launch parameters shared by the C-ABI layer (rpl_api.cpp) and the kernels (render.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rpl.h"
+
+namespace rpl {
+
+// One camera as the kernels see it.  Tiles are 8 x 4 pixels (one warp); tile_off / pix_off are the
+// camera's first tile / pixel inside one env.
+struct CamDev {
+    int32_t width, height, tiles_x, tile_off;
+    int32_t pix_off, mount;
+    float fx, fy, cx, cy, d_min, d_max;
+    float off_pos[3];
+    float off_quat[4];   // xyzw, normalised on the host
+};
+
+// Per-(env, link) and per-(env, camera) transforms computed once per render by the prep kernel.
+//   link_xf  [E*L*3] float4: rows of R^T (world -> link) with the link origin t in .w
+//   link_box [E*L*2] float4: world AABB of the link's mesh (lo, hi); far away when the link has none
+//   cam_xf   [E*C*4] float4: rows of R_c with the mounting link's origin in .w, then the mount
+//                            offset rotated into the world (R_l p_off) in the last float4
+struct PrepParams {
+    const float *poses;        // [E, L, 7]
+    const float4 *link_root;   // [RPL_MAX_LINKS * 2] link-frame root boxes (lo, hi)
+    float4 *link_xf;
+    float4 *link_box;
+    float4 *cam_xf;
+    int32_t E, L, C;
+    CamDev cams[RPL_MAX_CAMERAS];
+};
+
+struct RenderParams {
+    const float4 *tnodes;   // terrain BVH nodes (4 float4 each), root = node 0
+    const float4 *ttris;    // terrain triangles (3 float4 each)
+    const float4 *lnodes;   // all link BVH nodes
+    const float4 *ltris;    // all link triangles
+    const float4 *link_xf;
+    const float4 *link_box;
+    const float4 *cam_xf;
+    const float *intr;      // [E, C, 4] per-env (fx, fy, cx, cy) or null
+    int32_t E, L, C, tiles_per_env;
+    int32_t pix_per_env, depth_kind;
+    int32_t lroot[RPL_MAX_LINKS];   // root node of each link BVH in lnodes, -1 = no mesh
+    CamDev cams[RPL_MAX_CAMERAS];
+    // sensor model
+    int64_t step;
+    uint32_t env_offset, span;      // span = max_latency + 1
+    uint32_t seed0, seed1;
+    uint64_t drop_thr;              // floor(p_drop 2^32)
+    float sigma_abs, sigma_rel, fill;
+    int32_t sensor_on;
+    float *ring;                    // [E, span, pix_per_env] or null when span == 1
+    const int64_t *s_first;         // [E]
+    float *out;                     // [E, pix_per_env]
+    int32_t *err;                   // error word (bit 0: traversal stack overflow)
+    unsigned long long *counters;   // rpl_counters fields, or null
+};
+
+cudaError_t launch_prep(const PrepParams &p, cudaStream_t s);
+cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s);
+cudaError_t launch_set_first(int64_t *s_first, int32_t E, int64_t step, const uint8_t *mask, cudaStream_t s);
+
+// Depth of the traversal stack; scenes whose BVH is deeper are refused at build time.
+constexpr int kStackDepth = 64;
+
+}  // namespace rpl

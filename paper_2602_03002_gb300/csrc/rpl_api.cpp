@@ -1,0 +1,776 @@
+// rpl_api.cpp -- the C ABI (include/rpl.h): scenes, views, argument checks, device memory,
+// host/device pointer handling and kernel launches.  No torch types cross this boundary.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/rpl.h"
+#include "bvh.h"
+#include "render.h"
+
+using namespace rpl;
+
+namespace {
+
+thread_local std::string g_err;
+
+rpl_status fail(rpl_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+rpl_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? RPL_ERR_OUT_OF_MEMORY : RPL_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+// Makes `dev` current for the lifetime of the guard and restores the caller's device after.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t alloc(size_t n) {
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = n;
+        return cudaSuccess;
+    }
+    template <class T>
+    T *as() const {
+        return reinterpret_cast<T *>(p);
+    }
+};
+
+enum PtrKind { PTR_HOST, PTR_DEVICE, PTR_OTHER_DEVICE };
+
+PtrKind pointer_kind(const void *ptr, int device) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return PTR_HOST;
+    }
+    if (a.type == cudaMemoryTypeDevice) return a.device == device ? PTR_DEVICE : PTR_OTHER_DEVICE;
+    if (a.type == cudaMemoryTypeManaged) return PTR_DEVICE;
+    return PTR_HOST;
+}
+
+// Copies a host-or-device array to host memory.
+rpl_status to_host(const void *src, size_t bytes, int device, std::vector<char> &dst) {
+    dst.resize(bytes);
+    if (bytes == 0) return RPL_OK;
+    PtrKind k = pointer_kind(src, device);
+    if (k == PTR_HOST) {
+        std::memcpy(dst.data(), src, bytes);
+        return RPL_OK;
+    }
+    cudaError_t e = cudaMemcpy(dst.data(), src, bytes, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(e, "copying an input array to the host");
+    return RPL_OK;
+}
+
+void quat_normalise(const float in[4], float out[4]) {
+    double n = std::sqrt((double)in[0] * in[0] + (double)in[1] * in[1] + (double)in[2] * in[2] +
+                         (double)in[3] * in[3]);
+    for (int k = 0; k < 4; ++k) out[k] = n > 0 ? (float)(in[k] / n) : (k == 3 ? 1.f : 0.f);
+}
+
+}  // namespace
+
+struct rpl_scene {
+    int device = 0;
+    rpl_scene_opts opts{};
+    DevBuf t_nodes, t_tris;
+    int64_t t_n_nodes = 0, t_n_tris = 0;
+    int32_t t_depth = 0;
+    std::vector<HostBvh> links;      // indexed by link id
+    std::vector<bool> has_link;
+    DevBuf l_nodes, l_tris, l_roots;
+    int32_t l_root[RPL_MAX_LINKS];
+    int64_t l_n_nodes = 0, l_n_tris = 0;
+    int32_t l_depth = 0;
+    bool frozen = false;
+    int views = 0;
+    std::mutex mu;
+};
+
+struct rpl_view {
+    rpl_scene *scene = nullptr;
+    int32_t E = 0, L = 0, C = 0;
+    rpl_camera cams[RPL_MAX_CAMERAS];
+    int64_t cam_off[RPL_MAX_CAMERAS + 1];
+    int32_t tile_off[RPL_MAX_CAMERAS + 1];
+    int64_t P = 0;
+    bool cams_set = false;
+    rpl_sensor_params sensor{};
+    DevBuf link_xf, link_box, cam_xf, intr, ring, s_first, mask_stage, pose_stage, out_stage;
+    int32_t *err_host = nullptr;   // mapped pinned word written by the kernels
+    int32_t *err_dev = nullptr;
+    bool has_last = false;
+    int64_t last_step = 0;
+    bool need_first = true;        // s_first must be set by the next render
+    cudaStream_t last_stream = nullptr;
+    // optional timing of the traversal kernel: event pairs recorded around each launch
+    static constexpr int kTimingSlots = 256;
+    bool timing = false;
+    cudaEvent_t ev[2 * kTimingSlots] = {};
+    int64_t n_timed = 0;
+};
+
+extern "C" {
+
+RPL_API int32_t rpl_version(void) { return 1; }
+
+RPL_API const char *rpl_last_error(void) { return g_err.c_str(); }
+
+RPL_API rpl_status rpl_scene_create(const float *verts, int64_t n_verts, const int32_t *tris, int64_t n_tris,
+                                    const rpl_scene_opts *opts, rpl_scene_t *out) {
+    if (!out) return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: out is NULL");
+    *out = nullptr;
+    if (n_verts < 0 || n_tris < 0) return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: negative size");
+    if (n_tris > 0 && (!verts || !tris)) return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: NULL mesh array");
+    if (n_tris > (int64_t)0x7FFFFFF0) return fail(RPL_ERR_CAPACITY, "rpl_scene_create: too many triangles");
+    rpl_scene_opts o{};
+    if (opts) o = *opts;
+    if (o.bvh_kind != RPL_BVH2) return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: unknown bvh_kind %d", o.bvh_kind);
+    if (o.max_leaf_size < 0 || o.max_leaf_size > 8)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: max_leaf_size must be 0..8");
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess || o.device < 0 || o.device >= n_dev) {
+        cudaGetLastError();
+        return fail(RPL_ERR_NOT_FOUND, "rpl_scene_create: no CUDA device %d", o.device);
+    }
+    DeviceGuard g(o.device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "rpl_scene_create: cudaSetDevice");
+
+    std::vector<char> hv, ht;
+    rpl_status st = to_host(verts, (size_t)n_verts * 3 * sizeof(float), o.device, hv);
+    if (st != RPL_OK) return st;
+    st = to_host(tris, (size_t)n_tris * 3 * sizeof(int32_t), o.device, ht);
+    if (st != RPL_OK) return st;
+
+    rpl_scene *s = new (std::nothrow) rpl_scene();
+    if (!s) return fail(RPL_ERR_OUT_OF_MEMORY, "rpl_scene_create: host allocation");
+    s->device = o.device;
+    s->opts = o;
+    s->links.resize(RPL_MAX_LINKS);
+    s->has_link.assign(RPL_MAX_LINKS, false);
+    for (int l = 0; l < RPL_MAX_LINKS; ++l) s->l_root[l] = -1;
+    {
+        HostBvh bvh;
+        int rc = build_bvh2(reinterpret_cast<const float *>(hv.data()), n_verts,
+                            reinterpret_cast<const int32_t *>(ht.data()), n_tris, o.max_leaf_size, o.build_threads,
+                            &bvh);
+        if (rc == -1) {
+            delete s;
+            return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: vertex index out of range");
+        }
+        if (rc != 0) {
+            delete s;
+            return fail(RPL_ERR_OUT_OF_MEMORY, "rpl_scene_create: host allocation during the BVH build");
+        }
+        if (bvh.depth >= kStackDepth) {
+            delete s;
+            return fail(RPL_ERR_CAPACITY, "rpl_scene_create: BVH depth %d exceeds %d", bvh.depth, kStackDepth);
+        }
+        s->t_n_nodes = (int64_t)bvh.nodes.size();
+        s->t_n_tris = (int64_t)bvh.tris.size();
+        s->t_depth = bvh.depth;
+        cudaError_t e = s->t_nodes.alloc(bvh.nodes.size() * sizeof(BvhNode));
+        if (e == cudaSuccess) e = s->t_tris.alloc(std::max<size_t>(bvh.tris.size(), 1) * sizeof(BvhTri));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(s->t_nodes.p, bvh.nodes.data(), bvh.nodes.size() * sizeof(BvhNode), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !bvh.tris.empty())
+            e = cudaMemcpy(s->t_tris.p, bvh.tris.data(), bvh.tris.size() * sizeof(BvhTri), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            delete s;
+            return cuda_fail(e, "rpl_scene_create: uploading the terrain BVH");
+        }
+    }
+    *out = s;
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_link_mesh_add(rpl_scene_t s, int32_t link_id, const float *verts, int64_t n_verts,
+                                     const int32_t *tris, int64_t n_tris) {
+    if (!s) return fail(RPL_ERR_INVALID_ARG, "rpl_link_mesh_add: scene is NULL");
+    if (link_id < 0 || link_id >= RPL_MAX_LINKS)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_link_mesh_add: link_id %d outside 0..%d", link_id, RPL_MAX_LINKS - 1);
+    if (n_verts < 0 || n_tris < 0) return fail(RPL_ERR_INVALID_ARG, "rpl_link_mesh_add: negative size");
+    if (n_tris > 0 && (!verts || !tris)) return fail(RPL_ERR_INVALID_ARG, "rpl_link_mesh_add: NULL mesh array");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->frozen) return fail(RPL_ERR_INVALID_ARG, "rpl_link_mesh_add: scene is frozen by rpl_view_create");
+    DeviceGuard g(s->device);
+    std::vector<char> hv, ht;
+    rpl_status st = to_host(verts, (size_t)n_verts * 3 * sizeof(float), s->device, hv);
+    if (st != RPL_OK) return st;
+    st = to_host(tris, (size_t)n_tris * 3 * sizeof(int32_t), s->device, ht);
+    if (st != RPL_OK) return st;
+    HostBvh bvh;
+    int rc = build_bvh2(reinterpret_cast<const float *>(hv.data()), n_verts,
+                        reinterpret_cast<const int32_t *>(ht.data()), n_tris, s->opts.max_leaf_size, 1, &bvh);
+    if (rc == -1) return fail(RPL_ERR_INVALID_ARG, "rpl_link_mesh_add: vertex index out of range");
+    if (rc != 0) return fail(RPL_ERR_OUT_OF_MEMORY, "rpl_link_mesh_add: host allocation");
+    if (bvh.depth >= kStackDepth) return fail(RPL_ERR_CAPACITY, "rpl_link_mesh_add: BVH too deep");
+    s->links[link_id] = std::move(bvh);
+    s->has_link[link_id] = n_tris > 0;
+    return RPL_OK;
+}
+
+static rpl_status freeze(rpl_scene *s) {
+    if (s->frozen) return RPL_OK;
+    std::vector<BvhNode> nodes;
+    std::vector<BvhTri> tris;
+    std::vector<float> roots(RPL_MAX_LINKS * 8, 0.f);
+    int32_t depth = 0;
+    for (int l = 0; l < RPL_MAX_LINKS; ++l) {
+        float *r = roots.data() + 8 * l;
+        if (!s->has_link[l]) {
+            s->l_root[l] = -1;
+            r[0] = r[1] = r[2] = 1.f;   // inverted: lo > hi marks "no mesh"
+            r[4] = r[5] = r[6] = -1.f;
+            continue;
+        }
+        const HostBvh &b = s->links[l];
+        const int32_t nb = (int32_t)nodes.size(), tb = (int32_t)tris.size();
+        for (BvhNode n : b.nodes) {
+            n.child0 = n.child0 >= 0 ? n.child0 + nb : ~(~n.child0 + tb);
+            n.child1 = n.child1 >= 0 ? n.child1 + nb : ~(~n.child1 + tb);
+            nodes.push_back(n);
+        }
+        tris.insert(tris.end(), b.tris.begin(), b.tris.end());
+        s->l_root[l] = nb;
+        depth = std::max(depth, b.depth);
+        for (int a = 0; a < 3; ++a) {
+            r[a] = b.root_lo[a];
+            r[4 + a] = b.root_hi[a];
+        }
+    }
+    if (nodes.empty()) nodes.push_back(BvhNode{});
+    if (tris.empty()) tris.push_back(BvhTri{});
+    cudaError_t e = s->l_nodes.alloc(nodes.size() * sizeof(BvhNode));
+    if (e == cudaSuccess) e = s->l_tris.alloc(tris.size() * sizeof(BvhTri));
+    if (e == cudaSuccess) e = s->l_roots.alloc(roots.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(s->l_nodes.p, nodes.data(), nodes.size() * sizeof(BvhNode), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->l_tris.p, tris.data(), tris.size() * sizeof(BvhTri), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->l_roots.p, roots.data(), roots.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "uploading the link BVHs");
+    s->l_n_nodes = 0;
+    s->l_n_tris = 0;
+    for (int l = 0; l < RPL_MAX_LINKS; ++l)
+        if (s->has_link[l]) {
+            s->l_n_nodes += (int64_t)s->links[l].nodes.size();
+            s->l_n_tris += (int64_t)s->links[l].tris.size();
+        }
+    s->l_depth = depth;
+    s->links.clear();
+    s->links.shrink_to_fit();
+    s->frozen = true;
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_scene_info_get(rpl_scene_t s, rpl_scene_info *info) {
+    if (!s || !info) return fail(RPL_ERR_INVALID_ARG, "rpl_scene_info_get: NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    info->terrain_tris = s->t_n_tris;
+    info->terrain_nodes = s->t_n_nodes;
+    info->terrain_bytes = s->t_n_nodes * (int64_t)sizeof(BvhNode) + s->t_n_tris * (int64_t)sizeof(BvhTri);
+    info->terrain_depth = s->t_depth;
+    int n = 0;
+    int64_t ln = 0, lt = 0;
+    int32_t ld = 0;
+    for (int l = 0; l < RPL_MAX_LINKS; ++l)
+        if (s->has_link[l]) {
+            ++n;
+            if (!s->frozen) {
+                ln += (int64_t)s->links[l].nodes.size();
+                lt += (int64_t)s->links[l].tris.size();
+                ld = std::max(ld, s->links[l].depth);
+            }
+        }
+    if (s->frozen) {
+        ln = s->l_n_nodes;
+        lt = s->l_n_tris;
+        ld = s->l_depth;
+    }
+    info->n_links = n;
+    info->link_tris = lt;
+    info->link_nodes = ln;
+    info->link_bytes = ln * (int64_t)sizeof(BvhNode) + lt * (int64_t)sizeof(BvhTri);
+    info->link_depth = ld;
+    info->frozen = s->frozen ? 1 : 0;
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_bvh_build_host(const float *verts, int64_t n_verts, const int32_t *tris, int64_t n_tris,
+                                      int32_t max_leaf, int32_t threads, void *nodes_out, int64_t nodes_cap,
+                                      void *tris_out, int64_t *n_nodes, int32_t *depth) {
+    if (n_verts < 0 || n_tris < 0 || !n_nodes || !depth || (n_tris > 0 && (!verts || !tris)))
+        return fail(RPL_ERR_INVALID_ARG, "rpl_bvh_build_host: bad argument");
+    if (max_leaf < 0 || max_leaf > 8) return fail(RPL_ERR_INVALID_ARG, "rpl_bvh_build_host: max_leaf 0..8");
+    HostBvh b;
+    int rc = build_bvh2(verts, n_verts, tris, n_tris, max_leaf, threads, &b);
+    if (rc == -1) return fail(RPL_ERR_INVALID_ARG, "rpl_bvh_build_host: vertex index out of range");
+    if (rc != 0) return fail(RPL_ERR_OUT_OF_MEMORY, "rpl_bvh_build_host: host allocation");
+    *n_nodes = (int64_t)b.nodes.size();
+    *depth = b.depth;
+    if (nodes_out) {
+        if (nodes_cap < (int64_t)b.nodes.size()) return fail(RPL_ERR_CAPACITY, "rpl_bvh_build_host: nodes_cap too small");
+        std::memcpy(nodes_out, b.nodes.data(), b.nodes.size() * sizeof(BvhNode));
+    }
+    if (tris_out && n_tris > 0) std::memcpy(tris_out, b.tris.data(), b.tris.size() * sizeof(BvhTri));
+    return RPL_OK;
+}
+
+RPL_API void rpl_scene_destroy(rpl_scene_t s) {
+    if (!s) return;
+    DeviceGuard g(s->device);
+    delete s;
+}
+
+RPL_API rpl_status rpl_view_create(rpl_scene_t s, int32_t n_envs, int32_t n_links, rpl_view_t *out) {
+    if (!out) return fail(RPL_ERR_INVALID_ARG, "rpl_view_create: out is NULL");
+    *out = nullptr;
+    if (!s) return fail(RPL_ERR_INVALID_ARG, "rpl_view_create: scene is NULL");
+    if (n_envs < 0 || n_links < 1) return fail(RPL_ERR_INVALID_ARG, "rpl_view_create: n_envs >= 0 and n_links >= 1");
+    if (n_links > RPL_MAX_LINKS) return fail(RPL_ERR_CAPACITY, "rpl_view_create: n_links > %d", RPL_MAX_LINKS);
+    std::lock_guard<std::mutex> lk(s->mu);
+    DeviceGuard g(s->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "rpl_view_create: cudaSetDevice");
+    rpl_status st = freeze(s);
+    if (st != RPL_OK) return st;
+    rpl_view *v = new (std::nothrow) rpl_view();
+    if (!v) return fail(RPL_ERR_OUT_OF_MEMORY, "rpl_view_create: host allocation");
+    v->scene = s;
+    v->E = n_envs;
+    v->L = n_links;
+    const size_t EL = (size_t)n_envs * n_links;
+    cudaError_t e = v->link_xf.alloc(EL * 3 * sizeof(float4));
+    if (e == cudaSuccess) e = v->link_box.alloc(EL * 2 * sizeof(float4));
+    if (e == cudaSuccess) e = v->s_first.alloc((size_t)n_envs * sizeof(int64_t));
+    if (e == cudaSuccess) e = v->mask_stage.alloc((size_t)n_envs);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&v->err_host, sizeof(int32_t), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *v->err_host = 0;
+        e = cudaHostGetDevicePointer((void **)&v->err_dev, v->err_host, 0);
+    }
+    if (e != cudaSuccess) {
+        if (v->err_host) cudaFreeHost(v->err_host);
+        delete v;
+        return cuda_fail(e, "rpl_view_create: allocating per-env state");
+    }
+    v->sensor.out_dtype = RPL_OUT_F32;
+    s->views++;
+    *out = v;
+    return RPL_OK;
+}
+
+static rpl_status alloc_ring(rpl_view *v) {
+    const int64_t span = (int64_t)v->sensor.max_latency + 1;
+    if (!v->cams_set || span <= 1) {
+        v->ring.release();
+        return RPL_OK;
+    }
+    cudaError_t e = v->ring.alloc((size_t)v->E * span * v->P * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, "allocating the latency ring buffer");
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_cameras_set(rpl_view_t v, const rpl_camera *cams, int32_t n_cams, const float *per_env_intr) {
+    if (!v || !cams) return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: NULL argument");
+    if (n_cams < 1) return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: need at least one camera");
+    if (n_cams > RPL_MAX_CAMERAS) return fail(RPL_ERR_CAPACITY, "rpl_cameras_set: more than %d cameras", RPL_MAX_CAMERAS);
+    int64_t off = 0;
+    int32_t toff = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        const rpl_camera &k = cams[c];
+        if (k.width <= 0 || k.height <= 0 || k.width > 16384 || k.height > 16384)
+            return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: camera %d size %dx%d", c, k.width, k.height);
+        if (!(k.fx != 0.f) || !(k.fy != 0.f) || !std::isfinite(k.fx) || !std::isfinite(k.fy))
+            return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: camera %d has fx or fy 0", c);
+        if (k.mount_link < 0 || k.mount_link >= v->L)
+            return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: camera %d mount_link %d outside 0..%d", c,
+                        k.mount_link, v->L - 1);
+        if (!(k.d_min <= k.d_max) || !(k.d_max > 0.f) || !std::isfinite(k.d_max))
+            return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: camera %d needs 0 < d_max, d_min <= d_max", c);
+        v->cam_off[c] = off;
+        v->tile_off[c] = toff;
+        off += (int64_t)k.width * k.height;
+        toff += ((k.width + 7) / 8) * ((k.height + 3) / 4);
+    }
+    if (off >= (int64_t)1 << 31) return fail(RPL_ERR_CAPACITY, "rpl_cameras_set: too many pixels per env");
+    DeviceGuard g(v->scene->device);
+    for (int c = 0; c < n_cams; ++c) v->cams[c] = cams[c];
+    v->cam_off[n_cams] = off;
+    v->tile_off[n_cams] = toff;
+    v->C = n_cams;
+    v->P = off;
+    v->cams_set = true;
+    cudaError_t e = v->cam_xf.alloc((size_t)v->E * n_cams * 4 * sizeof(float4));
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_cameras_set: allocating camera transforms");
+    if (per_env_intr) {
+        const size_t bytes = (size_t)v->E * n_cams * 4 * sizeof(float);
+        std::vector<char> h;
+        rpl_status st = to_host(per_env_intr, bytes, v->scene->device, h);
+        if (st != RPL_OK) return st;
+        e = v->intr.alloc(bytes);
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(v->intr.p, h.data(), bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "rpl_cameras_set: per-env intrinsics");
+        const float *k = reinterpret_cast<const float *>(h.data());
+        for (size_t i = 0; i < (size_t)v->E * n_cams; ++i)
+            if (!(k[4 * i] != 0.f) || !(k[4 * i + 1] != 0.f))
+                return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: per-env intrinsics have fx or fy 0");
+    } else {
+        v->intr.release();
+    }
+    v->out_stage.release();
+    v->has_last = false;
+    v->need_first = true;
+    return alloc_ring(v);
+}
+
+RPL_API rpl_status rpl_sensor_set(rpl_view_t v, const rpl_sensor_params *prm) {
+    if (!v || !prm) return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_set: NULL argument");
+    if (prm->max_latency < 0 || prm->max_latency > 15)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_set: max_latency must be 0..15");
+    if (!(prm->p_drop >= 0.f && prm->p_drop <= 1.f))
+        return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_set: p_drop must be in [0, 1]");
+    if (!(prm->sigma_abs >= 0.f) || !(prm->sigma_rel >= 0.f) || !std::isfinite(prm->sigma_abs) ||
+        !std::isfinite(prm->sigma_rel) || !std::isfinite(prm->fill))
+        return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_set: sigmas must be finite and >= 0, fill finite");
+    if (prm->depth_kind != RPL_DEPTH_Z && prm->depth_kind != RPL_DEPTH_RANGE)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_set: unknown depth_kind");
+    if (prm->out_dtype != RPL_OUT_F32) return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_set: unknown out_dtype");
+    DeviceGuard g(v->scene->device);
+    v->sensor = *prm;
+    v->has_last = false;
+    v->need_first = true;
+    return alloc_ring(v);
+}
+
+RPL_API rpl_status rpl_view_layout(rpl_view_t v, int64_t *cam_offsets, int64_t *total) {
+    if (!v) return fail(RPL_ERR_INVALID_ARG, "rpl_view_layout: view is NULL");
+    if (!v->cams_set) return fail(RPL_ERR_INVALID_ARG, "rpl_view_layout: cameras not set");
+    if (cam_offsets)
+        for (int c = 0; c <= v->C; ++c) cam_offsets[c] = v->cam_off[c];
+    if (total) *total = v->P;
+    return RPL_OK;
+}
+
+static void fill_cams(const rpl_view *v, CamDev *out) {
+    for (int c = 0; c < v->C; ++c) {
+        const rpl_camera &k = v->cams[c];
+        CamDev &d = out[c];
+        d.width = k.width;
+        d.height = k.height;
+        d.tiles_x = (k.width + 7) / 8;
+        d.tile_off = v->tile_off[c];
+        d.pix_off = (int32_t)v->cam_off[c];
+        d.mount = k.mount_link;
+        d.fx = k.fx;
+        d.fy = k.fy;
+        d.cx = k.cx;
+        d.cy = k.cy;
+        d.d_min = k.d_min;
+        d.d_max = k.d_max;
+        for (int a = 0; a < 3; ++a) d.off_pos[a] = k.offset_pos[a];
+        quat_normalise(k.offset_quat_xyzw, d.off_quat);
+    }
+}
+
+static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int64_t env_offset, float *out_dev,
+                          cudaStream_t st, bool count, unsigned long long *counters_dev) {
+    rpl_scene *s = v->scene;
+    cudaError_t e;
+    if (v->need_first) {
+        e = launch_set_first(v->s_first.as<int64_t>(), v->E, step, nullptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the sensor-state reset");
+        v->need_first = false;
+    }
+    PrepParams pp{};
+    pp.poses = poses_dev;
+    pp.link_root = s->l_roots.as<const float4>();
+    pp.link_xf = v->link_xf.as<float4>();
+    pp.link_box = v->link_box.as<float4>();
+    pp.cam_xf = v->cam_xf.as<float4>();
+    pp.E = v->E;
+    pp.L = v->L;
+    pp.C = v->C;
+    fill_cams(v, pp.cams);
+    e = launch_prep(pp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the prep kernel");
+
+    RenderParams rp{};
+    rp.tnodes = s->t_nodes.as<const float4>();
+    rp.ttris = s->t_tris.as<const float4>();
+    rp.lnodes = s->l_nodes.as<const float4>();
+    rp.ltris = s->l_tris.as<const float4>();
+    rp.link_xf = v->link_xf.as<const float4>();
+    rp.link_box = v->link_box.as<const float4>();
+    rp.cam_xf = v->cam_xf.as<const float4>();
+    rp.intr = v->intr.p ? v->intr.as<const float>() : nullptr;
+    rp.E = v->E;
+    rp.L = v->L;
+    rp.C = v->C;
+    rp.tiles_per_env = v->tile_off[v->C];
+    rp.pix_per_env = (int32_t)v->P;
+    rp.depth_kind = v->sensor.depth_kind;
+    for (int l = 0; l < RPL_MAX_LINKS; ++l) rp.lroot[l] = l < v->L ? s->l_root[l] : -1;
+    std::memcpy(rp.cams, pp.cams, sizeof(pp.cams));
+    const rpl_sensor_params &sp = v->sensor;
+    rp.step = step;
+    rp.env_offset = (uint32_t)env_offset;
+    rp.span = (uint32_t)sp.max_latency + 1u;
+    rp.seed0 = sp.seed[0];
+    rp.seed1 = sp.seed[1];
+    double thr = std::floor((double)sp.p_drop * 4294967296.0);
+    rp.drop_thr = (uint64_t)std::min(std::max(thr, 0.0), 4294967296.0);
+    rp.sigma_abs = sp.sigma_abs;
+    rp.sigma_rel = sp.sigma_rel;
+    rp.fill = sp.fill;
+    rp.sensor_on = (sp.sigma_abs != 0.f || sp.sigma_rel != 0.f || sp.p_drop != 0.f || sp.max_latency != 0) ? 1 : 0;
+    rp.ring = rp.span > 1 ? v->ring.as<float>() : nullptr;
+    rp.s_first = v->s_first.as<const int64_t>();
+    rp.out = out_dev;
+    rp.err = v->err_dev;
+    rp.counters = counters_dev;
+    const int slot = (int)(v->n_timed % rpl_view::kTimingSlots);
+    if (v->timing) cudaEventRecord(v->ev[2 * slot], st);
+    e = launch_render(rp, count, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the render kernel");
+    if (v->timing) {
+        cudaEventRecord(v->ev[2 * slot + 1], st);
+        v->n_timed++;
+    }
+    v->last_stream = st;
+    return RPL_OK;
+}
+
+static rpl_status check_render_args(rpl_view *v, const float *poses, int64_t env_offset, void *out) {
+    if (!v) return fail(RPL_ERR_INVALID_ARG, "rpl_render: view is NULL");
+    if (!v->cams_set) return fail(RPL_ERR_INVALID_ARG, "rpl_render: cameras not set");
+    if (v->E > 0 && (!poses || !out)) return fail(RPL_ERR_INVALID_ARG, "rpl_render: NULL poses or output");
+    if (env_offset < 0 || env_offset + (int64_t)v->E > ((int64_t)1 << 32))
+        return fail(RPL_ERR_INVALID_ARG, "rpl_render: env_offset + n_envs must lie in [0, 2^32]");
+    if (((uintptr_t)poses & 3) || ((uintptr_t)out & 3))
+        return fail(RPL_ERR_INVALID_ARG, "rpl_render: poses and output must be 4-byte aligned");
+    if (*v->err_host != 0)
+        return fail(RPL_ERR_DEVICE_FAULT, "rpl_render: an earlier kernel on this view recorded error 0x%x "
+                    "(traversal stack overflow); call rpl_sync", *v->err_host);
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_render(rpl_view_t v, const float *poses, int64_t step, int64_t env_offset, void *out,
+                              void *stream) {
+    rpl_status st = check_render_args(v, poses, env_offset, out);
+    if (st != RPL_OK) return st;
+    if (v->has_last && step != v->last_step && step != v->last_step + 1)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_render: step %lld after %lld; steps must advance by 0 or 1 "
+                    "(rpl_view_reset restarts)", (long long)step, (long long)v->last_step);
+    if (v->E == 0) {
+        v->has_last = true;
+        v->last_step = step;
+        return RPL_OK;
+    }
+    rpl_scene *s = v->scene;
+    DeviceGuard g(s->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "rpl_render: cudaSetDevice");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const size_t pose_bytes = (size_t)v->E * v->L * 7 * sizeof(float);
+    const size_t out_bytes = (size_t)v->E * v->P * sizeof(float);
+    // While the stream is being captured into a graph the buffers must be device memory: no
+    // pointer queries are issued then.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(cs, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusNone;
+    }
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    const PtrKind pk = capturing ? PTR_DEVICE : pointer_kind(poses, s->device);
+    const PtrKind ok = capturing ? PTR_DEVICE : pointer_kind(out, s->device);
+    if (pk == PTR_OTHER_DEVICE || ok == PTR_OTHER_DEVICE)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_render: a buffer lives on another GPU than the scene");
+    const float *pd = poses;
+    float *od = reinterpret_cast<float *>(out);
+    cudaError_t e;
+    if (pk == PTR_HOST) {
+        if (v->pose_stage.bytes < pose_bytes) {
+            e = v->pose_stage.alloc(pose_bytes);
+            if (e != cudaSuccess) return cuda_fail(e, "rpl_render: allocating the pose staging buffer");
+        }
+        e = cudaMemcpyAsync(v->pose_stage.p, poses, pose_bytes, cudaMemcpyHostToDevice, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "rpl_render: copying poses to the device");
+        pd = v->pose_stage.as<const float>();
+    }
+    if (ok == PTR_HOST) {
+        if (v->out_stage.bytes < out_bytes) {
+            e = v->out_stage.alloc(out_bytes);
+            if (e != cudaSuccess) return cuda_fail(e, "rpl_render: allocating the output staging buffer");
+        }
+        od = v->out_stage.as<float>();
+    }
+    st = enqueue(v, pd, step, env_offset, od, cs, false, nullptr);
+    if (st != RPL_OK) return st;
+    v->has_last = true;
+    v->last_step = step;
+    if (ok == PTR_HOST) {
+        e = cudaMemcpyAsync(out, od, out_bytes, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) return cuda_fail(e, "rpl_render: copying depth to the host");
+    }
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_render_counters(rpl_view_t v, const float *poses, int64_t step, int64_t env_offset,
+                                       void *out, void *stream, rpl_counters *counters) {
+    rpl_status st = check_render_args(v, poses, env_offset, out);
+    if (st != RPL_OK) return st;
+    if (!counters) return fail(RPL_ERR_INVALID_ARG, "rpl_render_counters: counters is NULL");
+    std::memset(counters, 0, sizeof(*counters));
+    if (v->E == 0) return RPL_OK;
+    rpl_scene *s = v->scene;
+    DeviceGuard g(s->device);
+    if (pointer_kind(poses, s->device) != PTR_DEVICE || pointer_kind(out, s->device) != PTR_DEVICE)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_render_counters: poses and output must be device memory");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    DevBuf cnt;
+    cudaError_t e = cnt.alloc(6 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt.p, 0, 6 * sizeof(unsigned long long), cs);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_render_counters: counter buffer");
+    st = enqueue(v, poses, step, env_offset, reinterpret_cast<float *>(out), cs, true, cnt.as<unsigned long long>());
+    if (st != RPL_OK) return st;
+    unsigned long long h[6];
+    e = cudaMemcpyAsync(h, cnt.p, sizeof h, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_render_counters: reading counters");
+    counters->rays = h[0];
+    counters->terrain_nodes = h[1];
+    counters->terrain_tris = h[2];
+    counters->link_boxes = h[3];
+    counters->link_nodes = h[4];
+    counters->link_tris = h[5];
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_view_reset(rpl_view_t v, const uint8_t *mask, int64_t step, void *stream) {
+    if (!v) return fail(RPL_ERR_INVALID_ARG, "rpl_view_reset: view is NULL");
+    if (mask == nullptr) {
+        v->has_last = true;
+        v->last_step = step - 1;
+        v->need_first = true;   // the next render (at `step`) sets every env's first step
+        return RPL_OK;
+    }
+    if (!v->has_last || step != v->last_step + 1)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_view_reset: with a mask, step must be the next step to render");
+    if (v->need_first) return RPL_OK;   // the next render restarts every env at `step` anyway
+    if (v->E == 0) return RPL_OK;
+    DeviceGuard g(v->scene->device);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const uint8_t *md = mask;
+    cudaError_t e;
+    if (pointer_kind(mask, v->scene->device) == PTR_HOST) {
+        e = cudaMemcpyAsync(v->mask_stage.p, mask, (size_t)v->E, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) return cuda_fail(e, "rpl_view_reset: copying the mask");
+        md = v->mask_stage.as<const uint8_t>();
+    }
+    e = launch_set_first(v->s_first.as<int64_t>(), v->E, step, md, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_view_reset: launch");
+    v->last_stream = cs;
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_sync(rpl_view_t v) {
+    if (!v) return fail(RPL_ERR_INVALID_ARG, "rpl_sync: view is NULL");
+    DeviceGuard g(v->scene->device);
+    cudaError_t e = cudaStreamSynchronize(v->last_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_sync");
+    int32_t w = *(volatile int32_t *)v->err_host;
+    if (w != 0) {
+        *v->err_host = 0;
+        return fail(RPL_ERR_DEVICE_FAULT, "rpl_sync: a render kernel recorded error 0x%x (traversal stack overflow)", w);
+    }
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_view_timing(rpl_view_t v, int32_t enable) {
+    if (!v) return fail(RPL_ERR_INVALID_ARG, "rpl_view_timing: view is NULL");
+    DeviceGuard g(v->scene->device);
+    if (enable && !v->ev[0]) {
+        for (int i = 0; i < 2 * rpl_view::kTimingSlots; ++i) {
+            cudaError_t e = cudaEventCreate(&v->ev[i]);
+            if (e != cudaSuccess) return cuda_fail(e, "rpl_view_timing: cudaEventCreate");
+        }
+    }
+    v->timing = enable != 0;
+    v->n_timed = 0;
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_view_kernel_ms(rpl_view_t v, float *ms, int32_t max_n, int32_t *n_out) {
+    if (!v || !ms || !n_out || max_n < 0) return fail(RPL_ERR_INVALID_ARG, "rpl_view_kernel_ms: bad argument");
+    DeviceGuard g(v->scene->device);
+    const int64_t avail = std::min<int64_t>(v->n_timed, rpl_view::kTimingSlots);
+    const int64_t n = std::min<int64_t>(avail, max_n);
+    for (int64_t i = 0; i < n; ++i) {
+        const int slot = (int)((v->n_timed - n + i) % rpl_view::kTimingSlots);
+        cudaError_t e = cudaEventSynchronize(v->ev[2 * slot + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[i], v->ev[2 * slot], v->ev[2 * slot + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "rpl_view_kernel_ms");
+    }
+    *n_out = (int32_t)n;
+    return RPL_OK;
+}
+
+RPL_API void rpl_view_destroy(rpl_view_t v) {
+    if (!v) return;
+    {
+        DeviceGuard g(v->scene->device);
+        if (v->last_stream) cudaStreamSynchronize(v->last_stream);
+        if (v->err_host) cudaFreeHost(v->err_host);
+        for (int i = 0; i < 2 * rpl_view::kTimingSlots; ++i)
+            if (v->ev[i]) cudaEventDestroy(v->ev[i]);
+        std::lock_guard<std::mutex> lk(v->scene->mu);
+        v->scene->views--;
+        delete v;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,214 @@
+"""Host-side checks that need no GPU: the C ABI library loads and exports every declared symbol,
+fails cleanly without a device, and its BVH builder keeps the invariants the kernels rely on;
+the workload generator produces the stated sizes with cameras outside the robot."""
+import ctypes
+import re
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+from paper_2602_03002_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "rpl.h")) as f:
+        src = f.read()
+    return sorted(set(re.findall(r"RPL_API\s+[\w\s\*]+?\b(rpl_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(rpl_lib):
+    names = _declared()
+    assert len(names) >= 17
+    L = ctypes.CDLL(rpl_lib.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(rpl_lib.EXPORTS)
+    assert rpl_lib.lib().rpl_version() == 1
+
+
+def test_scene_create_fails_cleanly_without_gpu(rpl_lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(rpl_lib.RplError) as ei:
+        rpl_lib.Scene(np.zeros((3, 3), np.float32), np.array([[0, 1, 2]], np.int32))
+    assert ei.value.status == 4
+    assert rpl_lib.lib().rpl_render(None, None, 0, 0, None, None) == 1
+
+
+# --------------------------------------------------------------------------------------------------
+# BVH invariants
+# --------------------------------------------------------------------------------------------------
+def _child_box(n, k):
+    cx = n["c0x"] if k == 0 else n["c1x"]
+    cy = n["c0y"] if k == 0 else n["c1y"]
+    cz = n["c0z"] if k == 0 else n["c1z"]
+    return np.array([cx[0], cy[0], cz[0]]), np.array([cx[1], cy[1], cz[1]])
+
+
+def _check_bvh(verts, tris, max_leaf, rpl):
+    nodes, ltris, depth = rpl.rpl_bvh_build_host(verts, tris, max_leaf)
+    T = len(tris)
+    assert len(nodes) >= 1
+    assert np.array_equal(np.sort(ltris["id"]), np.arange(T))            # each triangle exactly once
+    if T:
+        orig = verts[tris[ltris["id"]]]                                    # leaf-ordered copies are exact
+        assert np.array_equal(ltris["v0"], orig[:, 0]) and np.array_equal(ltris["v1"], orig[:, 1])
+        assert np.array_equal(ltris["v2"], orig[:, 2])
+    covered = np.zeros(T, np.int32)
+    max_d = 0
+    stack = [(0, 1, None)]
+    while stack:
+        i, d, parent_box = stack.pop()
+        max_d = max(max_d, d)
+        n = nodes[i]
+        for k in range(2):
+            lo, hi = _child_box(n, k)
+            c, cnt = int(n["child"][k]), int(n["count"][k])
+            if parent_box is not None and c >= 0 or (parent_box is not None and cnt > 0):
+                assert np.all(lo >= parent_box[0]) and np.all(hi <= parent_box[1])   # child within parent
+            if c >= 0:
+                assert c > i                                               # acyclic: children come later
+                stack.append((c, d + 1, (lo, hi)))
+            else:
+                first = ~c
+                assert 0 <= cnt <= max(max_leaf, 1) or (T <= max_leaf)
+                covered[first:first + cnt] += 1
+                if cnt:
+                    p = np.concatenate([ltris["v0"][first:first + cnt], ltris["v1"][first:first + cnt],
+                                        ltris["v2"][first:first + cnt]])
+                    assert np.all(p >= lo) and np.all(p <= hi)             # padded box holds its triangles
+    assert np.all(covered == 1)
+    assert max_d <= depth
+    return nodes, ltris
+
+
+def _traverse(nodes, ltris, o, d):
+    """Closest hit by walking the node encoding (child >= 0 inner, < 0 leaf ~first with count)."""
+    best = np.inf
+    stack = [0]
+    inv = 1.0 / np.where(d == 0, 1e-30, d)
+    while stack:
+        n = nodes[stack.pop()]
+        for k in range(2):
+            lo, hi = _child_box(n, k)
+            t0, t1 = (lo - o) * inv, (hi - o) * inv
+            tin, tout = max(np.minimum(t0, t1).max(), 0.0), min(np.maximum(t0, t1).min(), best)
+            if tin > tout:
+                continue
+            c = int(n["child"][k])
+            if c >= 0:
+                stack.append(c)
+            else:
+                for j in range(~c, ~c + int(n["count"][k])):
+                    a, b, cc = (ltris[f][j].astype(np.float64) for f in ("v0", "v1", "v2"))
+                    e1, e2 = b - a, cc - a
+                    p = np.cross(d, e2)
+                    det = e1 @ p
+                    if abs(det) < 1e-15:
+                        continue
+                    s = o - a
+                    u = (s @ p) / det
+                    q = np.cross(s, e1)
+                    v = (d @ q) / det
+                    t = (e2 @ q) / det
+                    if u >= 0 and v >= 0 and u + v <= 1 and 0 < t < best:
+                        best = t
+    return best
+
+
+@pytest.mark.parametrize("kind", ["terrain", "box", "ellipsoid", "soup", "one", "empty"])
+@pytest.mark.parametrize("max_leaf", [1, 4, 8])
+def test_bvh_invariants_and_encoding(rpl_lib, kind, max_leaf):
+    rng = np.random.default_rng(7)
+    if kind == "terrain":
+        w = W.config_small(n_steps=1, n_envs=1)
+        v, t = w.terrain_verts, w.terrain_tris
+    elif kind == "box":
+        v, t = W.box_mesh((0.1, 0.2, 0.3), (0.05, 0, 0))
+    elif kind == "ellipsoid":
+        v, t = W.ellipsoid_mesh((0.2, 0.1, 0.3))
+    elif kind == "soup":
+        v = rng.uniform(-3, 3, (300, 3)).astype(np.float32)
+        t = rng.integers(0, 300, (400, 3)).astype(np.int32)
+    elif kind == "one":
+        v, t = np.eye(3, dtype=np.float32), np.array([[0, 1, 2]], np.int32)
+    else:
+        v, t = np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32)
+    nodes, ltris = _check_bvh(v, t, max_leaf, rpl_lib)
+    if len(t) == 0:
+        return
+    # the node encoding reaches the same closest hit as brute force
+    tris = v[t].astype(np.float64)
+    lo, hi = v.min(0), v.max(0)
+    for _ in range(25):
+        o = rng.uniform(lo - 1, hi + 1)
+        target = tris[rng.integers(len(tris))].mean(0)
+        d = target - o
+        d /= np.linalg.norm(d)
+        got = _traverse(nodes, ltris, o, d)
+        exp = np.inf
+        for a, b, c in tris:
+            e1, e2 = b - a, c - a
+            p = np.cross(d, e2)
+            det = e1 @ p
+            if abs(det) < 1e-15:
+                continue
+            s = o - a
+            uu = (s @ p) / det
+            q = np.cross(s, e1)
+            vv = (d @ q) / det
+            tt = (e2 @ q) / det
+            if uu >= 0 and vv >= 0 and uu + vv <= 1 and 0 < tt < exp:
+                exp = tt
+        assert got == exp
+
+
+def test_bvh_is_deterministic_across_thread_counts(rpl_lib):
+    w = W.config_small(n_steps=1, n_envs=1)
+    a = rpl_lib.rpl_bvh_build_host(w.terrain_verts, w.terrain_tris, 4, 1)
+    b = rpl_lib.rpl_bvh_build_host(w.terrain_verts, w.terrain_tris, 4, 8)
+    assert a[2] == b[2] and a[0].tobytes() == b[0].tobytes() and a[1].tobytes() == b[1].tobytes()
+
+
+def test_bvh_rejects_bad_indices(rpl_lib):
+    with pytest.raises(rpl_lib.RplError) as ei:
+        rpl_lib.rpl_bvh_build_host(np.zeros((3, 3), np.float32), np.array([[0, 1, 3]], np.int32))
+    assert ei.value.status == 1
+
+
+# --------------------------------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------------------------------
+def test_workload_sizes():
+    s = W.config_small()
+    assert len(s.terrain_tris) == 3200 and s.n_links == 20 and all(len(t) == 48 for t in s.link_tris)
+    assert s.rays_per_step == 8 * 2 * 32 * 24 == 12288
+    big = W.config_scale(n_envs=16, n_steps=1, tiles=2)
+    assert len(big.terrain_tris) == 2 * (2 * 8 / 0.05) ** 2 and big.n_links == 30
+    assert all(len(t) == 512 for t in big.link_tris)
+    assert big.sensor.max_latency == 3 and big.sensor.p_drop == 0.02 and big.sensor.sigma_abs == 0.01
+    u = W.config_uneven(n_envs=4, n_steps=1, tiles=1)
+    assert [c.width * c.height for c in u.cameras] == [4800, 4800, 1728, 1728]
+
+
+@pytest.mark.parametrize("cfg", ["small", "scale"])
+def test_cameras_start_outside_every_link(cfg):
+    w = W.config_small(n_steps=3) if cfg == "small" else W.config_scale(n_envs=64, n_steps=3, tiles=2)
+    for s in range(w.n_steps):
+        for e in range(w.n_envs):
+            P = w.poses[s, e].astype(np.float64)
+            for cam in w.cameras:
+                R = Rotation.from_quat(P[cam.mount_link, 3:]).as_matrix()
+                o = P[cam.mount_link, :3] + R @ np.asarray(cam.offset_pos)
+                for l, (lv, lt) in enumerate(zip(w.link_verts, w.link_tris)):
+                    Rl = Rotation.from_quat(P[l, 3:]).as_matrix()
+                    ol = Rl.T @ (o - P[l, :3])
+                    tri = lv[lt].astype(np.float64)
+                    n = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+                    side = np.einsum("ij,ij->i", n, ol - tri[:, 0])
+                    assert side.max() > 0, (s, e, l)     # in front of some face of the convex mesh
