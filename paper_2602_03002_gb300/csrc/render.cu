@@ -58,6 +58,34 @@ __device__ __forceinline__ void quat_rot(float x, float y, float z, float w, flo
 __device__ __forceinline__ float pad_lo(float v) { return v - (fabsf(v) * 0x1p-18f + 1e-5f); }
 __device__ __forceinline__ float pad_hi(float v) { return v + (fabsf(v) * 0x1p-18f + 1e-5f); }
 
+// World AABB of link l of env e (the link-frame root box moved by the link pose), padded outward.
+// Returns false for a link without a mesh.
+__device__ __forceinline__ bool link_world_box(const PrepParams &p, int64_t el, int l, const float R[9],
+                                               float lo_out[3], float hi_out[3]) {
+    const float *q = p.poses + 7 * el;
+    const float4 lo = p.link_root[2 * l], hi = p.link_root[2 * l + 1];
+    if (!(lo.x <= hi.x)) return false;
+    const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y), cz = 0.5f * (lo.z + hi.z);
+    const float hx = 0.5f * (hi.x - lo.x), hy = 0.5f * (hi.y - lo.y), hz = 0.5f * (hi.z - lo.z);
+    const float w[3] = {R[0] * cx + R[1] * cy + R[2] * cz + q[0], R[3] * cx + R[4] * cy + R[5] * cz + q[1],
+                        R[6] * cx + R[7] * cy + R[8] * cz + q[2]};
+    // slack covers the rounding of the centre/extent arithmetic above
+    const float ext[3] = {fabsf(R[0]) * hx + fabsf(R[1]) * hy + fabsf(R[2]) * hz + 1e-6f,
+                          fabsf(R[3]) * hx + fabsf(R[4]) * hy + fabsf(R[5]) * hz + 1e-6f,
+                          fabsf(R[6]) * hx + fabsf(R[7]) * hy + fabsf(R[8]) * hz + 1e-6f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo_out[a] = pad_lo(w[a] - ext[a]);
+        hi_out[a] = pad_hi(w[a] + ext[a]);
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool boxes_overlap(float alx, float ahx, float aly, float ahy, float alz, float ahz,
+                                              const float blo[3], const float bhi[3]) {
+    return alx <= bhi[0] && blo[0] <= ahx && aly <= bhi[1] && blo[1] <= ahy && alz <= bhi[2] && blo[2] <= ahz;
+}
+
 __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepParams p) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n_link = (int64_t)p.E * p.L;
@@ -66,27 +94,15 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
         const float *q = p.poses + 7 * i;
         float R[9];
         quat_rot(q[3], q[4], q[5], q[6], R);
-        const float tx = q[0], ty = q[1], tz = q[2];
-        p.link_xf[3 * i + 0] = make_float4(R[0], R[3], R[6], tx);
-        p.link_xf[3 * i + 1] = make_float4(R[1], R[4], R[7], ty);
-        p.link_xf[3 * i + 2] = make_float4(R[2], R[5], R[8], tz);
-        const float4 lo = p.link_root[2 * l], hi = p.link_root[2 * l + 1];
-        if (!(lo.x <= hi.x)) {
-            p.link_box[2 * i + 0] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
-            p.link_box[2 * i + 1] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
-            return;
+        p.link_xf[3 * i + 0] = make_float4(R[0], R[3], R[6], q[0]);
+        p.link_xf[3 * i + 1] = make_float4(R[1], R[4], R[7], q[1]);
+        p.link_xf[3 * i + 2] = make_float4(R[2], R[5], R[8], q[2]);
+        float lo[3], hi[3];
+        if (!link_world_box(p, i, l, R, lo, hi)) {
+            lo[0] = lo[1] = lo[2] = hi[0] = hi[1] = hi[2] = 1e30f;
         }
-        const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y), cz = 0.5f * (lo.z + hi.z);
-        const float hx = 0.5f * (hi.x - lo.x), hy = 0.5f * (hi.y - lo.y), hz = 0.5f * (hi.z - lo.z);
-        const float wx = R[0] * cx + R[1] * cy + R[2] * cz + tx;
-        const float wy = R[3] * cx + R[4] * cy + R[5] * cz + ty;
-        const float wz = R[6] * cx + R[7] * cy + R[8] * cz + tz;
-        // slack covers the rounding of the centre/extent arithmetic above
-        const float ex = fabsf(R[0]) * hx + fabsf(R[1]) * hy + fabsf(R[2]) * hz + 1e-6f;
-        const float ey = fabsf(R[3]) * hx + fabsf(R[4]) * hy + fabsf(R[5]) * hz + 1e-6f;
-        const float ez = fabsf(R[6]) * hx + fabsf(R[7]) * hy + fabsf(R[8]) * hz + 1e-6f;
-        p.link_box[2 * i + 0] = make_float4(pad_lo(wx - ex), pad_lo(wy - ey), pad_lo(wz - ez), 0.f);
-        p.link_box[2 * i + 1] = make_float4(pad_hi(wx + ex), pad_hi(wy + ey), pad_hi(wz + ez), 0.f);
+        p.link_box[2 * i + 0] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        p.link_box[2 * i + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
         return;
     }
     const int64_t j = i - n_link;
@@ -106,10 +122,94 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
     const float ox = Rl[0] * cam.off_pos[0] + Rl[1] * cam.off_pos[1] + Rl[2] * cam.off_pos[2];
     const float oy = Rl[3] * cam.off_pos[0] + Rl[4] * cam.off_pos[1] + Rl[5] * cam.off_pos[2];
     const float oz = Rl[6] * cam.off_pos[0] + Rl[7] * cam.off_pos[1] + Rl[8] * cam.off_pos[2];
-    p.cam_xf[4 * j + 0] = make_float4(Rc[0], Rc[1], Rc[2], q[0]);
-    p.cam_xf[4 * j + 1] = make_float4(Rc[3], Rc[4], Rc[5], q[1]);
-    p.cam_xf[4 * j + 2] = make_float4(Rc[6], Rc[7], Rc[8], q[2]);
-    p.cam_xf[4 * j + 3] = make_float4(ox, oy, oz, 0.f);
+    p.cam_xf[5 * j + 0] = make_float4(Rc[0], Rc[1], Rc[2], q[0]);
+    p.cam_xf[5 * j + 1] = make_float4(Rc[3], Rc[4], Rc[5], q[1]);
+    p.cam_xf[5 * j + 2] = make_float4(Rc[6], Rc[7], Rc[8], q[2]);
+    p.cam_xf[5 * j + 3] = make_float4(ox, oy, oz, 0.f);
+
+    // The camera's view volume: apex o, far face at z-depth d_max through the four corner pixels.
+    // Every pixel ray segment of this camera (z-depth or range) lies inside it.
+    float fx = cam.fx, fy = cam.fy, pcx = cam.cx, pcy = cam.cy;
+    if (p.intr) {
+        const float4 k = reinterpret_cast<const float4 *>(p.intr)[(int64_t)e * p.C + c];
+        fx = k.x; fy = k.y; pcx = k.z; pcy = k.w;
+    }
+    const float o[3] = {q[0] + ox, q[1] + oy, q[2] + oz};
+    float B[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float rx = ((k & 1) ? (float)(cam.width - 1) - pcx : -pcx) / fx;
+        const float ry = ((k & 2) ? (float)(cam.height - 1) - pcy : -pcy) / fy;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) B[k][a] = o[a] + cam.d_max * (Rc[3 * a] * rx + Rc[3 * a + 1] * ry + Rc[3 * a + 2]);
+    }
+    float flo[3], fhi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        flo[a] = fminf(fminf(o[a], fminf(B[0][a], B[1][a])), fminf(B[2][a], B[3][a]));
+        fhi[a] = fmaxf(fmaxf(o[a], fmaxf(B[0][a], B[1][a])), fmaxf(B[2][a], B[3][a]));
+        const float slack = 1e-3f + 1e-5f * fmaxf(fabsf(flo[a]), fabsf(fhi[a]));
+        flo[a] -= slack;
+        fhi[a] += slack;
+    }
+
+    // 1) links whose world AABB meets the view pyramid (4 side planes through the apex, far plane)
+    float N[4][3];
+    const int ring[4] = {0, 1, 3, 2};
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const float *a = B[ring[s]], *b = B[ring[(s + 1) & 3]];
+        const float u[3] = {a[0] - o[0], a[1] - o[1], a[2] - o[2]}, v[3] = {b[0] - o[0], b[1] - o[1], b[2] - o[2]};
+        float n[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+        // orient inward: towards the optical axis
+        if (n[0] * Rc[2] + n[1] * Rc[5] + n[2] * Rc[8] < 0.f) {
+            n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2];
+        }
+        N[s][0] = n[0]; N[s][1] = n[1]; N[s][2] = n[2];
+    }
+    uint64_t mask = 0;
+    for (int l = 0; l < p.L; ++l) {
+        if (p.lroot[l] < 0) continue;
+        const int64_t el = (int64_t)e * p.L + l;
+        const float *ql = p.poses + 7 * el;
+        float R[9], lo[3], hi[3];
+        quat_rot(ql[3], ql[4], ql[5], ql[6], R);
+        if (!link_world_box(p, el, l, R, lo, hi)) continue;
+        bool inside = true;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            // the box corner farthest along the inward normal must not be behind the plane
+            const float d = N[s][0] * ((N[s][0] >= 0.f ? hi[0] : lo[0]) - o[0]) +
+                            N[s][1] * ((N[s][1] >= 0.f ? hi[1] : lo[1]) - o[1]) +
+                            N[s][2] * ((N[s][2] >= 0.f ? hi[2] : lo[2]) - o[2]);
+            const float len = sqrtf(N[s][0] * N[s][0] + N[s][1] * N[s][1] + N[s][2] * N[s][2]);
+            inside &= d >= -1e-3f * len;
+        }
+        // far plane: the box corner nearest along the optical axis must lie within d_max
+        const float zn = Rc[2] * ((Rc[2] >= 0.f ? lo[0] : hi[0]) - o[0]) + Rc[5] * ((Rc[5] >= 0.f ? lo[1] : hi[1]) - o[1]) +
+                         Rc[8] * ((Rc[8] >= 0.f ? lo[2] : hi[2]) - o[2]);
+        inside &= zn <= cam.d_max + 1e-3f;
+        inside &= boxes_overlap(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2], flo, fhi);
+        if (inside) mask |= 1ull << l;
+    }
+
+    // 2) terrain entry node: descend while exactly one child's box meets the view volume's AABB and
+    //    that child is an inner node; nothing in the other subtrees can be hit by this camera's rays
+    int node = 0;
+    for (int depth = 0; depth < kStackDepth; ++depth) {
+        const float4 *n = p.tnodes + 4 * node;
+        const float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2);
+        const int4 n3 = __ldg(reinterpret_cast<const int4 *>(n + 3));
+        const bool h0 = !(n3.x < 0 && n3.z == 0) && boxes_overlap(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, flo, fhi);
+        const bool h1 = !(n3.y < 0 && n3.w == 0) && boxes_overlap(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, flo, fhi);
+        int next = -1;
+        if (h0 && !h1 && n3.x >= 0) next = n3.x;
+        if (h1 && !h0 && n3.y >= 0) next = n3.y;
+        if (next < 0) break;
+        node = next;
+    }
+    p.cam_xf[5 * j + 4] = make_float4(__uint_as_float((uint32_t)mask), __uint_as_float((uint32_t)(mask >> 32)),
+                                      __int_as_float(node), 0.f);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -267,7 +367,7 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
 }
 
 template <bool kCount>
-__global__ void __launch_bounds__(128) render_kernel(const __grid_constant__ RenderParams p) {
+__global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ RenderParams p) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (warp >= (int64_t)p.E * p.tiles_per_env) return;
@@ -287,8 +387,11 @@ __global__ void __launch_bounds__(128) render_kernel(const __grid_constant__ Ren
         const float4 k = __ldg(reinterpret_cast<const float4 *>(p.intr) + (int64_t)e * p.C + c);
         fx = k.x; fy = k.y; cx = k.z; cy = k.w;
     }
-    const float4 *cx4 = p.cam_xf + 4 * ((int64_t)e * p.C + c);
+    const float4 *cx4 = p.cam_xf + 5 * ((int64_t)e * p.C + c);
     const float4 R0 = __ldg(cx4), R1 = __ldg(cx4 + 1), R2 = __ldg(cx4 + 2), OF = __ldg(cx4 + 3);
+    const float4 CV = __ldg(cx4 + 4);
+    const uint64_t link_mask = ((uint64_t)__float_as_uint(CV.y) << 32) | __float_as_uint(CV.x);
+    const int entry = __float_as_int(CV.z);
     const float rx = __fdiv_rn((float)x - cx, fx), ry = __fdiv_rn((float)y - cy, fy);
     const float inv_n = 1.0f / sqrtf(rx * rx + ry * ry + 1.0f);
     const float ux = rx * inv_n, uy = ry * inv_n, uz = inv_n;
@@ -306,9 +409,11 @@ __global__ void __launch_bounds__(128) render_kernel(const __grid_constant__ Ren
     Ray ray;
     make_ray(ray, base, off, d);
 
-    // 1) dynamic robot bodies: rays move into each link frame (o_b = R^T (o - t), d_b = R^T d)
+    // 1) dynamic robot bodies inside this camera's view volume: rays move into each link frame
+    //    (o_b = R^T (o - t), d_b = R^T d)
 #pragma unroll 1
-    for (int l = 0; l < p.L; ++l) {
+    for (uint64_t mk = link_mask; mk; mk &= mk - 1) {
+        const int l = __ffsll((long long)mk) - 1;
         const int root = p.lroot[l];
         if (root < 0) continue;
         const int64_t el = (int64_t)e * p.L + l;
@@ -328,7 +433,7 @@ __global__ void __launch_bounds__(128) render_kernel(const __grid_constant__ Ren
         ok &= traverse<false, kCount>(p.lnodes, p.ltris, root, lr, tmax, hit, cnt_l);
     }
     // 2) static terrain, bounded by the closest body hit
-    ok &= traverse<true, kCount>(p.tnodes, p.ttris, 0, ray, tmax, hit, cnt_t);
+    ok &= traverse<true, kCount>(p.tnodes, p.ttris, entry, ray, tmax, hit, cnt_t);
     if (!ok) atomicOr(p.err, 1);
 
     float z = hit ? fminf(m * tmax, cam.d_max) : cam.d_max;
@@ -387,6 +492,7 @@ __global__ void set_first_kernel(int64_t *s_first, int32_t E, int64_t step, cons
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s) {
     const int64_t n = (int64_t)p.E * (p.L + p.C);
     if (n == 0) return cudaSuccess;
+    (void)cudaGetLastError();   // report only this launch's error, not a stale one
     prep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
@@ -395,6 +501,7 @@ cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
     const int64_t warps = (int64_t)p.E * p.tiles_per_env;
     if (warps == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((warps + 3) / 4);
+    (void)cudaGetLastError();
     if (count)
         render_kernel<true><<<blocks, 128, 0, s>>>(p);
     else
@@ -404,6 +511,7 @@ cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
 
 cudaError_t launch_set_first(int64_t *s_first, int32_t E, int64_t step, const uint8_t *mask, cudaStream_t s) {
     if (E == 0) return cudaSuccess;
+    (void)cudaGetLastError();
     set_first_kernel<<<(E + 255) / 256, 256, 0, s>>>(s_first, E, step, mask);
     return cudaGetLastError();
 }

@@ -20,15 +20,20 @@ struct CamDev {
 // Per-(env, link) and per-(env, camera) transforms computed once per render by the prep kernel.
 //   link_xf  [E*L*3] float4: rows of R^T (world -> link) with the link origin t in .w
 //   link_box [E*L*2] float4: world AABB of the link's mesh (lo, hi); far away when the link has none
-//   cam_xf   [E*C*4] float4: rows of R_c with the mounting link's origin in .w, then the mount
-//                            offset rotated into the world (R_l p_off) in the last float4
+//   cam_xf   [E*C*5] float4: rows of R_c with the mounting link's origin in .w; the mount offset
+//                            rotated into the world (R_l p_off); then (bits of the 64-bit mask of
+//                            links inside the camera's view volume, low and high word, bits of the
+//                            terrain entry node, 0)
 struct PrepParams {
     const float *poses;        // [E, L, 7]
     const float4 *link_root;   // [RPL_MAX_LINKS * 2] link-frame root boxes (lo, hi)
+    const float4 *tnodes;      // terrain BVH nodes
+    const float *intr;         // [E, C, 4] per-env intrinsics or null
     float4 *link_xf;
     float4 *link_box;
     float4 *cam_xf;
     int32_t E, L, C;
+    int32_t lroot[RPL_MAX_LINKS];
     CamDev cams[RPL_MAX_CAMERAS];
 };
 

@@ -443,7 +443,7 @@ RPL_API rpl_status rpl_cameras_set(rpl_view_t v, const rpl_camera *cams, int32_t
     v->C = n_cams;
     v->P = off;
     v->cams_set = true;
-    cudaError_t e = v->cam_xf.alloc((size_t)v->E * n_cams * 4 * sizeof(float4));
+    cudaError_t e = v->cam_xf.alloc((size_t)v->E * n_cams * 5 * sizeof(float4));
     if (e != cudaSuccess) return cuda_fail(e, "rpl_cameras_set: allocating camera transforms");
     if (per_env_intr) {
         const size_t bytes = (size_t)v->E * n_cams * 4 * sizeof(float);
@@ -527,6 +527,9 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
     PrepParams pp{};
     pp.poses = poses_dev;
     pp.link_root = s->l_roots.as<const float4>();
+    pp.tnodes = s->t_nodes.as<const float4>();
+    pp.intr = v->intr.p ? v->intr.as<const float>() : nullptr;
+    for (int l = 0; l < RPL_MAX_LINKS; ++l) pp.lroot[l] = l < v->L ? s->l_root[l] : -1;
     pp.link_xf = v->link_xf.as<float4>();
     pp.link_box = v->link_box.as<float4>();
     pp.cam_xf = v->cam_xf.as<float4>();

@@ -4,8 +4,11 @@ Small workload (8 envs x 2 cams x 32x24, 3,200-tri terrain, 20 box links): full 
 steps, sensor off and on.  Edge cases: ragged tiles, uneven cameras, per-env intrinsics, empty
 terrain, zero envs, links without meshes, range depth, graph capture, host buffers, env sharding.
 """
+import math
+
 import numpy as np
 import pytest
+from scipy.spatial.transform import Rotation
 
 import oracle
 from conftest import compare_depth
@@ -246,4 +249,34 @@ def test_counters(cuda, rpl_lib):
     assert torch.equal(out, plain)
     assert c["rays"] == w.rays_per_step
     assert c["terrain_nodes"] >= c["rays"] and c["terrain_tris"] > 0
-    assert c["link_boxes"] == w.rays_per_step * w.n_links
+    assert 0 < c["link_boxes"] < w.rays_per_step * w.n_links      # links outside the view volume are culled
+
+
+def test_max_cameras_and_links(cuda, rpl_lib):
+    """RPL_MAX_CAMERAS cameras of different sizes and RPL_MAX_LINKS links in one view."""
+    w = W.config_small(n_steps=1, n_envs=3)
+    rng = np.random.default_rng(9)
+    n_links = rpl_lib.RPL_MAX_LINKS
+    extra = n_links - w.n_links
+    P = w.poses[0]
+    # the extra links are small boxes floating around each env's robot
+    add = np.zeros((3, extra, 7), np.float32)
+    add[..., :3] = P[:, :1, :3] + rng.uniform(-1.2, 1.2, (3, extra, 3)).astype(np.float32)
+    add[..., 2] = P[:, :1, 2] - rng.uniform(0.2, 0.9, (3, extra)).astype(np.float32)
+    add[..., 3:] = np.asarray([Rotation.random(random_state=k).as_quat() for k in range(3 * extra)],
+                              np.float32).reshape(3, extra, 4)
+    w.poses = np.concatenate([P, add], axis=1)[None]
+    for k in range(extra):
+        v, t = W.box_mesh(rng.uniform(0.03, 0.12, 3), (0, 0, 0), subdiv=1 + k % 2)
+        w.link_verts.append(v)
+        w.link_tris.append(t)
+    torso = w.cameras[0].mount_link
+    w.cameras = [W.pinhole(5 + 3 * c, 4 + 2 * c, 70.0 + 3 * c, 50.0, torso, (0.1 * math.cos(c), 0.1 * math.sin(c), 0.3),
+                           45.0 * c, 40.0 + 3 * c, 0.1, 3.0) for c in range(rpl_lib.RPL_MAX_CAMERAS)]
+    outs, _, _ = _render_seq(cuda, rpl_lib, w, [0])
+    osc = oracle.OracleScene.from_workload(w)
+    rays = oracle.all_rays(w.cameras, w.n_envs)
+    ref = osc.render(w.cameras, w.poses, 0, rays, w.sensor)
+    compare_depth(outs[0], ref["depth"], ref["flags"], "max sizes")
+    with pytest.raises(rpl_lib.RplError):
+        rpl_lib.View(rpl_lib.Scene.from_workload(W.config_small(n_steps=1)), 2, n_links + 1)
