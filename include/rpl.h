@@ -225,6 +225,40 @@ RPL_API rpl_status rpl_view_kernel_ms(rpl_view_t view, float *ms, int32_t max_n,
 
 RPL_API void rpl_view_destroy(rpl_view_t view);
 
+/* ---------------------------------------------------------------------------------------------
+ * Rendering without allocating (the paper has no counterpart: this serves callers of the library)
+ * ------------------------------------------------------------------------------------------- */
+
+/* Size of the library's fixed device scratch array used by rpl_render_static_scratch. */
+#define RPL_STATIC_SCRATCH_BYTES (8 << 20)
+
+/* Render like rpl_render, but without allocating anything, for callers that cannot call cudaMalloc
+ * where they render: for example code running under a framework whose caching allocator owns the
+ * device memory, or a real-time loop where an allocation (which may synchronise the device) is not
+ * acceptable.  The per-call scratch (per-env link transforms and boxes, per-env camera poses) lives
+ * in one fixed __device__ array of RPL_STATIC_SCRATCH_BYTES inside the library, which every GPU
+ * that loads the library keeps until the process exits; a call needs
+ * 80 * n_envs * (n_links + n_cams) + 16 bytes of it and returns CAPACITY when that exceeds the
+ * array (about 3,270 envs with 30 links and 2 cameras).
+ *   scene       a frozen scene (rpl_view_create has been called on it once), read only
+ *   cams        host array of n_cams cameras (1..RPL_MAX_CAMERAS), as for rpl_cameras_set
+ *   link_poses  device, [n_envs, n_links, 7] float32
+ *   sensor      NULL (clip only) or a sensor with max_latency == 0: noise, clip and dropout are
+ *               applied, keyed by (env_offset + env, camera, pixel, step); latency needs a view
+ *   depth_out   device, n_envs * (sum of camera pixels) float32, cameras packed per env
+ *   stream      cudaStream_t (NULL = legacy default stream)
+ * The first call on a device looks up the device address of the array (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every call shares the
+ * array and it keeps the last call's contents: each call rewrites all of it that it reads, and
+ * clears its error word, but calls whose work overlaps on the GPU (other streams, other threads)
+ * race on it and must be serialised by the caller.  The call only enqueues work.
+ * Errors: INVALID_ARG (unfrozen scene, bad counts, cameras or sensor, max_latency != 0), CAPACITY,
+ * CUDA. */
+RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const rpl_camera *cams, int32_t n_cams,
+                                             int32_t n_envs, int32_t n_links, const float *link_poses,
+                                             const rpl_sensor_params *sensor, int64_t step,
+                                             int64_t env_offset, float *depth_out, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 RPL_API const char *rpl_last_error(void);
 

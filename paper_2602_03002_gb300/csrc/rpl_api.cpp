@@ -15,6 +15,7 @@
 #include "../../include/rpl.h"
 #include "bvh.h"
 #include "render.h"
+#include "scene_access.h"
 
 using namespace rpl;
 
@@ -777,3 +778,23 @@ RPL_API void rpl_view_destroy(rpl_view_t v) {
 }
 
 }  // extern "C"
+
+namespace rpl {
+
+bool scene_inputs(const rpl_scene *s, SceneInputs *out) {
+    if (!s) return false;
+    std::lock_guard<std::mutex> lk(const_cast<rpl_scene *>(s)->mu);
+    if (!s->frozen) return false;
+    out->device = s->device;
+    out->tnodes = s->t_nodes.as<const float4>();
+    out->ttris = s->t_tris.as<const float4>();
+    out->lnodes = s->l_nodes.as<const float4>();
+    out->ltris = s->l_tris.as<const float4>();
+    out->link_root = s->l_roots.as<const float4>();
+    for (int l = 0; l < RPL_MAX_LINKS; ++l) out->lroot[l] = s->l_root[l];
+    return true;
+}
+
+rpl_status set_error(rpl_status st, const char *msg) { return fail(st, "%s", msg); }
+
+}  // namespace rpl

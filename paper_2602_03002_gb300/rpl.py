@@ -63,7 +63,7 @@ class rpl_counters(ctypes.Structure):
 EXPORTS = ["rpl_bvh_build_host", "rpl_scene_create", "rpl_link_mesh_add", "rpl_scene_info_get", "rpl_scene_destroy", "rpl_view_create",
            "rpl_cameras_set", "rpl_sensor_set", "rpl_view_layout", "rpl_render", "rpl_view_reset", "rpl_sync",
            "rpl_render_counters", "rpl_view_timing", "rpl_view_kernel_ms", "rpl_view_destroy", "rpl_last_error",
-           "rpl_version"]
+           "rpl_version", "rpl_render_static_scratch"]
 
 _lib = None
 
@@ -96,6 +96,7 @@ def lib() -> ctypes.CDLL:
         "rpl_view_destroy": ([P], None),
         "rpl_last_error": ([], ctypes.c_char_p),
         "rpl_version": ([], I32),
+        "rpl_render_static_scratch": ([P, P, I32, I32, I32, P, P, I64, I64, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -245,6 +246,15 @@ def rpl_view_kernel_ms(view: int, max_n: int = 256):
     n = ctypes.c_int32()
     _check(lib().rpl_view_kernel_ms(view, buf, int(max_n), ctypes.byref(n)))
     return [buf[i] for i in range(n.value)]
+
+
+def rpl_render_static_scratch(scene: int, cams: Sequence, n_envs: int, n_links: int, poses, out, sensor=None,
+                              step: int = 0, env_offset: int = 0, stream=None):
+    """Render into `out` without allocating (scratch in the library's fixed device array)."""
+    arr = (rpl_camera * len(cams))(*[_camera_struct(c) for c in cams])
+    sen = None if sensor is None else ctypes.byref(_sensor_struct(sensor))
+    _check(lib().rpl_render_static_scratch(scene, arr, len(cams), int(n_envs), int(n_links), _ptr(poses), sen,
+                                           int(step), int(env_offset), _ptr(out), _stream_handle(stream)))
 
 
 def rpl_view_destroy(view: int):
