@@ -61,12 +61,15 @@ typedef enum { RPL_DEPTH_Z = 0, RPL_DEPTH_RANGE = 1 } rpl_depth_kind;
 typedef enum { RPL_OUT_F32 = 0 } rpl_out_dtype;
 
 /* Scene options.  device: CUDA ordinal; bvh_kind: rpl_bvh_kind; max_leaf_size: triangles per BVH
- * leaf (1..8, 0 = default 4); build_threads: host threads for the BVH build (0 = all cores). */
+ * leaf (1..8, 0 = default 4); build_threads: host threads for the BVH build (0 = all cores);
+ * sah_node_cost: surface-area-heuristic cost of visiting a node relative to testing a triangle
+ * (0 = default 1; larger values give fewer, bigger leaves). */
 typedef struct {
     int32_t device;
     int32_t bvh_kind;
     int32_t max_leaf_size;
     int32_t build_threads;
+    float sah_node_cost;
 } rpl_scene_opts;
 
 /* Pinhole camera.  Pixel (x, y), 0 <= x < width, 0 <= y < height, has the camera-frame ray

@@ -40,7 +40,8 @@ struct HostBvh {
 // whatever the thread count.  Child boxes are padded outward by max(|x| 2^-20, 1e-6) per bound, so
 // that FP32 slab tests stay conservative for rays whose origin carries FP32 rounding.
 // Returns 0, or -1 on a bad vertex index, -2 on allocation failure.
+// node_cost: SAH cost of visiting a node relative to testing one triangle (larger -> bigger leaves).
 int build_bvh2(const float *verts, int64_t n_verts, const int32_t *tris, int64_t n_tris,
-               int max_leaf, int n_threads, HostBvh *out);
+               int max_leaf, int n_threads, HostBvh *out, double node_cost = 1.0);
 
 }  // namespace rpl

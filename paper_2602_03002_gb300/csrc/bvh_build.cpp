@@ -19,7 +19,7 @@ namespace {
 
 constexpr int kBins = 16;
 constexpr int kMedianDepth = 32;        // below this depth splits become object medians
-constexpr double kTraversalCost = 1.0;  // SAH cost of visiting one node, relative to one triangle
+constexpr double kDefaultNodeCost = 1.0;  // SAH cost of visiting one node, relative to one triangle
 
 struct Box {
     float lo[3], hi[3];
@@ -178,7 +178,8 @@ struct Deferred {
 
 class Builder {
 public:
-    Builder(const Prims &P, int32_t *ref, int max_leaf) : P_(P), ref_(ref), max_leaf_(max_leaf) {}
+    Builder(const Prims &P, int32_t *ref, int max_leaf, double node_cost)
+        : P_(P), ref_(ref), max_leaf_(max_leaf), node_cost_(node_cost) {}
 
     // Top phase when defer_below > 0: ranges at or under the threshold are recorded, not built.
     ChildRef build(int64_t b0, int64_t b1, int depth, const Box &box, const Box &cbox,
@@ -206,7 +207,7 @@ public:
             }
             BinResult r = best_split(bins, cbox);
             double leaf_cost = box.half_area() * (double)n;
-            double split_cost = r.axis >= 0 ? kTraversalCost * box.half_area() + r.cost
+            double split_cost = r.axis >= 0 ? node_cost_ * box.half_area() + r.cost
                                              : std::numeric_limits<double>::infinity();
             if (n <= max_leaf_ && leaf_cost <= split_cost) return leaf(b0, b1, box);
             if (r.axis >= 0) {
@@ -299,12 +300,14 @@ private:
     const Prims &P_;
     int32_t *ref_;
     int max_leaf_;
+    double node_cost_;
 };
 
 }  // namespace
 
 int build_bvh2(const float *verts, int64_t n_verts, const int32_t *tris, int64_t n_tris, int max_leaf,
-               int n_threads, HostBvh *out) {
+               int n_threads, HostBvh *out, double node_cost) {
+    if (!(node_cost > 0.0)) node_cost = kDefaultNodeCost;
     if (max_leaf < 1) max_leaf = 4;
     if (max_leaf > 8) max_leaf = 8;
     if (n_threads <= 0) n_threads = (int)std::max(1u, std::thread::hardware_concurrency());
@@ -345,7 +348,7 @@ int build_bvh2(const float *verts, int64_t n_verts, const int32_t *tris, int64_t
     BvhNode root{};
     if (n_tris <= max_leaf) {
         // the root stays an inner node: child 0 holds every triangle, child 1 is empty
-        Builder b(P, ref.data(), max_leaf);
+        Builder b(P, ref.data(), max_leaf, node_cost);
         Box box, cbox;
         b.bounds(0, n_tris, box, cbox);
         ChildRef l;
@@ -365,7 +368,7 @@ int build_bvh2(const float *verts, int64_t n_verts, const int32_t *tris, int64_t
             out->root_hi[a] = box.hi[a];
         }
     } else {
-        Builder top(P, ref.data(), max_leaf);
+        Builder top(P, ref.data(), max_leaf, node_cost);
         Box box, cbox;
         top.bounds(0, n_tris, box, cbox);
         for (int a = 0; a < 3; ++a) {
@@ -388,7 +391,7 @@ int build_bvh2(const float *verts, int64_t n_verts, const int32_t *tris, int64_t
                 size_t i = next.fetch_add(1);
                 if (i >= deferred.size()) break;
                 const Deferred &d = deferred[i];
-                sub[i] = new Builder(P, ref.data(), max_leaf);
+                sub[i] = new Builder(P, ref.data(), max_leaf, node_cost);
                 sub_root[i] = sub[i]->build(d.begin, d.end, d.depth, d.box, d.cbox, 0, nullptr, -1, 0, 1);
             }
         };

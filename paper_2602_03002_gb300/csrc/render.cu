@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <climits>
+
 #include "render.h"
 
 namespace rpl {
@@ -208,8 +210,19 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
         if (next < 0) break;
         node = next;
     }
+    // 3) latency of this (env, camera, step): k = (w0 (Lmax + 1)) >> 32 from the word with pixel field
+    //    0xFFFFFFFF; source step s' = max(s - k, first step since reset); stored as s - s'
+    uint32_t delta = 0;
+    if (p.span > 1) {
+        const uint4 wl = sensor_words(p.env_offset + (uint32_t)e, (uint32_t)c, 0xFFFFFFFFu, p.step, p.seed0, p.seed1);
+        int64_t src = p.step - (int64_t)__umulhi(wl.x, p.span);
+        const int64_t first = p.s_first[e];
+        if (src < first) src = first;
+        if (src > p.step) src = p.step;
+        delta = (uint32_t)(p.step - src);
+    }
     p.cam_xf[5 * j + 4] = make_float4(__uint_as_float((uint32_t)mask), __uint_as_float((uint32_t)(mask >> 32)),
-                                      __int_as_float(node), 0.f);
+                                      __int_as_float(node), __uint_as_float(delta));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -313,56 +326,91 @@ __device__ __forceinline__ void leaf(const float4 *__restrict__ tris, int first,
     }
 }
 
+// During traversal a leaf child is carried as ~((first << 3) | (count - 1)) (always negative, since
+// scenes hold fewer than 2^28 - 1 triangles and leaves at most 8); kDone marks an exhausted stack.
+constexpr int kDone = INT_MIN;
+
+__device__ __forceinline__ int leaf_ref(int child, int count) { return ~((~child << 3) | (count - 1)); }
+
 // Closest hit below tmax in one BVH; tmax shrinks to the hit distance.  Returns false when the stack
 // would overflow (never for scenes accepted at build time).
+//
+// Inner nodes and leaves are handled in two phases (Aila and Laine, "Understanding the Efficiency of
+// Ray Traversal on GPUs", HPG 2009): a lane that meets a leaf postpones it and keeps descending
+// while any lane of the warp has not found a leaf yet, then the warp tests its leaves together, so
+// triangle tests run with most lanes active instead of one lane at a time.
 template <bool kSplit, bool kCount>
 __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const float4 *__restrict__ tris, int root,
                                          const Ray &r, float &tmax, bool &hit, Counts &cnt) {
     int stack_node[kStackDepth];
     float stack_t[kStackDepth];
     int sp = 0;
-    int cur = root;
-#pragma unroll 1
-    for (;;) {
-        const float4 *n = nodes + 4 * cur;
-        const float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2);
-        const int4 n3 = __ldg(reinterpret_cast<const int4 *>(n + 3));
-        if (kCount) ++cnt.nodes;
-        float t0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmax);
-        float t1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmax);
-        if (t0 != CUDART_INF_F && n3.x < 0) {
-            leaf<kSplit, kCount>(tris, ~n3.x, n3.z, r, tmax, hit, cnt);
-            t0 = CUDART_INF_F;
-            if (t1 > tmax) t1 = CUDART_INF_F;
-        }
-        if (t1 != CUDART_INF_F && n3.y < 0) {
-            leaf<kSplit, kCount>(tris, ~n3.y, n3.w, r, tmax, hit, cnt);
-            t1 = CUDART_INF_F;
-            if (t0 > tmax) t0 = CUDART_INF_F;
-        }
-        const bool h0 = t0 != CUDART_INF_F, h1 = t1 != CUDART_INF_F;
-        if (h0 && h1) {
-            const bool first0 = t0 <= t1;
-            if (sp == kStackDepth) return false;
-            stack_node[sp] = first0 ? n3.y : n3.x;
-            stack_t[sp] = first0 ? t1 : t0;
-            ++sp;
-            cur = first0 ? n3.x : n3.y;
-            continue;
-        }
-        if (h0) { cur = n3.x; continue; }
-        if (h1) { cur = n3.y; continue; }
-        // pop the nearest pending subtree that still starts before the bound
-        bool found = false;
+    bool ok = true;
+    int cur = root;      // >= 0 inner node, < 0 leaf reference, kDone nothing left
+    int pending = 0;     // postponed leaf reference, 0 = none
+    // the nearest pending entry that still starts before the bound
+    auto pop = [&]() -> int {
         while (sp > 0) {
             --sp;
-            if (stack_t[sp] <= tmax) {
-                cur = stack_node[sp];
-                found = true;
-                break;
+            if (stack_t[sp] <= tmax) return stack_node[sp];
+        }
+        return kDone;
+    };
+#pragma unroll 1
+    for (;;) {
+#pragma unroll 1
+        while (cur >= 0) {
+            const float4 *n = nodes + 4 * cur;
+            const float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2);
+            const int4 n3 = __ldg(reinterpret_cast<const int4 *>(n + 3));
+            if (kCount) ++cnt.nodes;
+            float t0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmax);
+            float t1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmax);
+            int e0 = n3.x, e1 = n3.y;
+            if (e0 < 0) {
+                if (n3.z == 0) t0 = CUDART_INF_F;
+                else e0 = leaf_ref(e0, n3.z);
+            }
+            if (e1 < 0) {
+                if (n3.w == 0) t1 = CUDART_INF_F;
+                else e1 = leaf_ref(e1, n3.w);
+            }
+            const bool h0 = t0 != CUDART_INF_F, h1 = t1 != CUDART_INF_F;
+            if (h0 && h1) {
+                const bool first0 = t0 <= t1;
+                if (sp == kStackDepth) {
+                    ok = false;
+                    cur = kDone;
+                    break;
+                }
+                stack_node[sp] = first0 ? e1 : e0;
+                stack_t[sp] = first0 ? t1 : t0;
+                ++sp;
+                cur = first0 ? e0 : e1;
+            } else if (h0) {
+                cur = e0;
+            } else if (h1) {
+                cur = e1;
+            } else {
+                cur = pop();
+            }
+            if (cur < 0 && cur != kDone && pending == 0) {
+                pending = cur;
+                cur = pop();
+            }
+            if (!__any_sync(__activemask(), pending == 0 && cur >= 0)) break;
+        }
+#pragma unroll 1
+        while (pending < 0) {
+            const int ref = ~pending;
+            leaf<kSplit, kCount>(tris, ref >> 3, (ref & 7) + 1, r, tmax, hit, cnt);
+            pending = 0;
+            if (cur < 0 && cur != kDone) {
+                pending = cur;
+                cur = pop();
             }
         }
-        if (!found) return true;
+        if (cur == kDone) return ok;
     }
 }
 
@@ -379,7 +427,9 @@ __global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ 
     const int t = r_tile - cam.tile_off;
     const int x = (t % cam.tiles_x) * 8 + (lane & 7);
     const int y = (t / cam.tiles_x) * 4 + (lane >> 3);
-    if (x >= cam.width || y >= cam.height) return;
+    // lanes outside a ragged tile still take part in the warp-wide reductions below
+    const bool active = x < cam.width && y < cam.height;
+    const int xs = min(x, cam.width - 1), ys = min(y, cam.height - 1);
 
     // BuildDepthRay: r = K^-1 [x, y, 1], d = R_c r / |r|, m = 1 / |r|
     float fx = cam.fx, fy = cam.fy, cx = cam.cx, cy = cam.cy;
@@ -390,9 +440,8 @@ __global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ 
     const float4 *cx4 = p.cam_xf + 5 * ((int64_t)e * p.C + c);
     const float4 R0 = __ldg(cx4), R1 = __ldg(cx4 + 1), R2 = __ldg(cx4 + 2), OF = __ldg(cx4 + 3);
     const float4 CV = __ldg(cx4 + 4);
-    const uint64_t link_mask = ((uint64_t)__float_as_uint(CV.y) << 32) | __float_as_uint(CV.x);
-    const int entry = __float_as_int(CV.z);
-    const float rx = __fdiv_rn((float)x - cx, fx), ry = __fdiv_rn((float)y - cy, fy);
+    const uint64_t cam_mask = ((uint64_t)__float_as_uint(CV.y) << 32) | __float_as_uint(CV.x);
+    const float rx = __fdiv_rn((float)xs - cx, fx), ry = __fdiv_rn((float)ys - cy, fy);
     const float inv_n = 1.0f / sqrtf(rx * rx + ry * ry + 1.0f);
     const float ux = rx * inv_n, uy = ry * inv_n, uz = inv_n;
     const float3 d = make_float3(R0.x * ux + R0.y * uy + R0.z * uz, R1.x * ux + R1.y * uy + R1.z * uz,
@@ -409,7 +458,52 @@ __global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ 
     Ray ray;
     make_ray(ray, base, off, d);
 
-    // 1) dynamic robot bodies inside this camera's view volume: rays move into each link frame
+    // The tile's reach: AABB of the 32 ray segments, padded for FP32 rounding.  The terrain walk
+    // starts at the deepest node below the camera's entry node that holds everything the tile can
+    // reach, and only links whose world box meets that AABB are tested.  Uniform across the warp.
+    float tlo[3], thi[3];
+    {
+        const float o3[3] = {base.x + off.x, base.y + off.y, base.z + off.z};
+        const float d3[3] = {d.x, d.y, d.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float far = o3[a] + d3[a] * tmax;
+            float lo = fminf(o3[a], far), hi = fmaxf(o3[a], far);
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, s));
+                hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, s));
+            }
+            const float slack = 1e-3f + 1e-5f * fmaxf(fabsf(lo), fabsf(hi));
+            tlo[a] = lo - slack;
+            thi[a] = hi + slack;
+        }
+    }
+    int entry = __float_as_int(CV.z);
+#pragma unroll 1
+    for (int depth = 0; depth < kStackDepth; ++depth) {
+        const float4 *n = p.tnodes + 4 * entry;
+        const float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2);
+        const int4 n3 = __ldg(reinterpret_cast<const int4 *>(n + 3));
+        const bool h0 = !(n3.x < 0 && n3.z == 0) && boxes_overlap(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tlo, thi);
+        const bool h1 = !(n3.y < 0 && n3.w == 0) && boxes_overlap(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tlo, thi);
+        int next = -1;
+        if (h0 && !h1 && n3.x >= 0) next = n3.x;
+        if (h1 && !h0 && n3.y >= 0) next = n3.y;
+        if (next < 0) break;
+        entry = next;
+    }
+    uint64_t link_mask = 0;
+#pragma unroll 1
+    for (uint64_t mk = cam_mask; mk; mk &= mk - 1) {
+        const int l = __ffsll((long long)mk) - 1;
+        const int64_t el = (int64_t)e * p.L + l;
+        const float4 blo = __ldg(p.link_box + 2 * el), bhi = __ldg(p.link_box + 2 * el + 1);
+        if (boxes_overlap(blo.x, bhi.x, blo.y, bhi.y, blo.z, bhi.z, tlo, thi)) link_mask |= 1ull << l;
+    }
+    if (!active) return;
+
+    // 1) dynamic robot bodies that the tile can reach: rays move into each link frame
     //    (o_b = R^T (o - t), d_b = R^T d)
 #pragma unroll 1
     for (uint64_t mk = link_mask; mk; mk &= mk - 1) {
@@ -447,11 +541,8 @@ __global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ 
         if (span > 1) {
             const int64_t slot = ((step % span) + span) % span;
             p.ring[((int64_t)e * span + slot) * p.pix_per_env + col] = z;
-            const uint4 wl = sensor_words(ge, (uint32_t)c, 0xFFFFFFFFu, step, p.seed0, p.seed1);
-            const int64_t k = (int64_t)__umulhi(wl.x, (uint32_t)span);
-            src = step - k;
-            const int64_t first = __ldg(p.s_first + e);
-            if (src < first) src = first;
+            // the latency of this (env, camera, step) was drawn by the prep kernel: src = step - delta
+            src = step - (int64_t)__float_as_uint(CV.w);
             if (src != step) {
                 const int64_t sslot = ((src % span) + span) % span;
                 z = p.ring[((int64_t)e * span + sslot) * p.pix_per_env + col];

@@ -23,7 +23,7 @@ struct CamDev {
 //   cam_xf   [E*C*5] float4: rows of R_c with the mounting link's origin in .w; the mount offset
 //                            rotated into the world (R_l p_off); then (bits of the 64-bit mask of
 //                            links inside the camera's view volume, low and high word, bits of the
-//                            terrain entry node, 0)
+//                            terrain entry node, bits of the latency delay s - s' of this step)
 struct PrepParams {
     const float *poses;        // [E, L, 7]
     const float4 *link_root;   // [RPL_MAX_LINKS * 2] link-frame root boxes (lo, hi)
@@ -35,6 +35,10 @@ struct PrepParams {
     int32_t E, L, C;
     int32_t lroot[RPL_MAX_LINKS];
     CamDev cams[RPL_MAX_CAMERAS];
+    // latency draw (span = max_latency + 1; 0 or 1 = none)
+    int64_t step;
+    const int64_t *s_first;
+    uint32_t env_offset, span, seed0, seed1;
 };
 
 struct RenderParams {

@@ -167,7 +167,8 @@ RPL_API rpl_status rpl_scene_create(const float *verts, int64_t n_verts, const i
     *out = nullptr;
     if (n_verts < 0 || n_tris < 0) return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: negative size");
     if (n_tris > 0 && (!verts || !tris)) return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: NULL mesh array");
-    if (n_tris > (int64_t)0x7FFFFFF0) return fail(RPL_ERR_CAPACITY, "rpl_scene_create: too many triangles");
+    // leaf references carry (first triangle << 3) in 31 bits during traversal
+    if (n_tris >= (int64_t)0x0FFFFFFF) return fail(RPL_ERR_CAPACITY, "rpl_scene_create: too many triangles");
     rpl_scene_opts o{};
     if (opts) o = *opts;
     if (o.bvh_kind != RPL_BVH2) return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: unknown bvh_kind %d", o.bvh_kind);
@@ -198,7 +199,7 @@ RPL_API rpl_status rpl_scene_create(const float *verts, int64_t n_verts, const i
         HostBvh bvh;
         int rc = build_bvh2(reinterpret_cast<const float *>(hv.data()), n_verts,
                             reinterpret_cast<const int32_t *>(ht.data()), n_tris, o.max_leaf_size, o.build_threads,
-                            &bvh);
+                            &bvh, o.sah_node_cost);
         if (rc == -1) {
             delete s;
             return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: vertex index out of range");
@@ -246,7 +247,8 @@ RPL_API rpl_status rpl_link_mesh_add(rpl_scene_t s, int32_t link_id, const float
     if (st != RPL_OK) return st;
     HostBvh bvh;
     int rc = build_bvh2(reinterpret_cast<const float *>(hv.data()), n_verts,
-                        reinterpret_cast<const int32_t *>(ht.data()), n_tris, s->opts.max_leaf_size, 1, &bvh);
+                        reinterpret_cast<const int32_t *>(ht.data()), n_tris, s->opts.max_leaf_size, 1, &bvh,
+                        s->opts.sah_node_cost);
     if (rc == -1) return fail(RPL_ERR_INVALID_ARG, "rpl_link_mesh_add: vertex index out of range");
     if (rc != 0) return fail(RPL_ERR_OUT_OF_MEMORY, "rpl_link_mesh_add: host allocation");
     if (bvh.depth >= kStackDepth) return fail(RPL_ERR_CAPACITY, "rpl_link_mesh_add: BVH too deep");
@@ -538,6 +540,12 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
     pp.L = v->L;
     pp.C = v->C;
     fill_cams(v, pp.cams);
+    pp.step = step;
+    pp.s_first = v->s_first.as<const int64_t>();
+    pp.env_offset = (uint32_t)env_offset;
+    pp.span = (uint32_t)v->sensor.max_latency + 1u;
+    pp.seed0 = v->sensor.seed[0];
+    pp.seed1 = v->sensor.seed[1];
     e = launch_prep(pp, st);
     if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the prep kernel");
 

@@ -32,7 +32,7 @@ class RplError(RuntimeError):
 
 class rpl_scene_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("bvh_kind", ctypes.c_int32), ("max_leaf_size", ctypes.c_int32),
-                ("build_threads", ctypes.c_int32)]
+                ("build_threads", ctypes.c_int32), ("sah_node_cost", ctypes.c_float)]
 
 
 class rpl_camera(ctypes.Structure):
@@ -153,10 +153,11 @@ def rpl_bvh_build_host(verts, tris, max_leaf: int = 0, threads: int = 0):
     return nodes, out_t, d.value
 
 
-def rpl_scene_create(verts, tris, device: int = 0, max_leaf_size: int = 0, build_threads: int = 0) -> int:
+def rpl_scene_create(verts, tris, device: int = 0, max_leaf_size: int = 0, build_threads: int = 0,
+                     sah_node_cost: float = 0.0) -> int:
     v = np.ascontiguousarray(verts, np.float32).reshape(-1, 3) if isinstance(verts, np.ndarray) else verts
     t = np.ascontiguousarray(tris, np.int32).reshape(-1, 3) if isinstance(tris, np.ndarray) else tris
-    opts = rpl_scene_opts(device, 0, max_leaf_size, build_threads)
+    opts = rpl_scene_opts(device, 0, max_leaf_size, build_threads, sah_node_cost)
     h = ctypes.c_void_p()
     _check(lib().rpl_scene_create(_ptr(v), int(v.shape[0]), _ptr(t), int(t.shape[0]), ctypes.byref(opts),
                                   ctypes.byref(h)))
@@ -271,9 +272,10 @@ def rpl_scene_destroy(scene: int):
 class Scene:
     """Terrain BVH (built once) plus link BVHs in their own frames."""
 
-    def __init__(self, terrain_verts, terrain_tris, device: int = 0, max_leaf_size: int = 0, build_threads: int = 0):
+    def __init__(self, terrain_verts, terrain_tris, device: int = 0, max_leaf_size: int = 0, build_threads: int = 0,
+                 sah_node_cost: float = 0.0):
         self.device = device
-        self.h = rpl_scene_create(terrain_verts, terrain_tris, device, max_leaf_size, build_threads)
+        self.h = rpl_scene_create(terrain_verts, terrain_tris, device, max_leaf_size, build_threads, sah_node_cost)
 
     @classmethod
     def from_workload(cls, w, device: int = 0, **kw) -> "Scene":
