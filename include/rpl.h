@@ -56,9 +56,16 @@ typedef struct rpl_view *rpl_view_t;     /* cameras, env count, sensor, per-env 
 #define RPL_MAX_CAMERAS 8
 #define RPL_MAX_LINKS 64
 
-typedef enum { RPL_BVH2 = 0 } rpl_bvh_kind;
+/* Terrain acceleration structure.  RPL_BVH2: binary BVH with FP32 child boxes (64-byte nodes).
+ * RPL_BVH8Q8: eight-wide BVH whose child boxes are quantised to 8 bits per bound on a per-node
+ * power-of-two grid and rounded outward (80-byte nodes); traversal and triangle tests stay FP32,
+ * so the depth is the same, only the culling is coarser.  Link meshes always use RPL_BVH2. */
+typedef enum { RPL_BVH2 = 0, RPL_BVH8Q8 = 1 } rpl_bvh_kind;
 typedef enum { RPL_DEPTH_Z = 0, RPL_DEPTH_RANGE = 1 } rpl_depth_kind;
-typedef enum { RPL_OUT_F32 = 0 } rpl_out_dtype;
+/* Output element type.  F32: float.  F16: IEEE half, round to nearest (max error 1/2 ulp of half:
+ * 0.98 mm in [2, 4) m).  U16: unsigned normalised over [0, d_max], q = rint(z / d_max * 65535)
+ * clamped to [0, 65535] (step d_max / 65535).  The latency ring buffer always holds FP32. */
+typedef enum { RPL_OUT_F32 = 0, RPL_OUT_F16 = 1, RPL_OUT_U16 = 2 } rpl_out_dtype;
 
 /* Scene options.  device: CUDA ordinal; bvh_kind: rpl_bvh_kind; max_leaf_size: triangles per BVH
  * leaf (1..8, 0 = default 4); build_threads: host threads for the BVH build (0 = all cores);
@@ -151,6 +158,12 @@ RPL_API rpl_status rpl_scene_info_get(rpl_scene_t scene, rpl_scene_info *info);
 RPL_API rpl_status rpl_bvh_build_host(const float *verts, int64_t n_verts, const int32_t *tris,
                                       int64_t n_tris, int32_t max_leaf, int32_t threads, void *nodes_out,
                                       int64_t nodes_cap, void *tris_out, int64_t *n_nodes, int32_t *depth);
+
+/* The same for the eight-wide quantised BVH (RPL_BVH8Q8): 80-byte nodes in the layout described at
+ * rpl_bvh_kind and leaf-ordered triangles; max_leaf 0..4. */
+RPL_API rpl_status rpl_bvh8_build_host(const float *verts, int64_t n_verts, const int32_t *tris,
+                                       int64_t n_tris, int32_t max_leaf, int32_t threads, void *nodes_out,
+                                       int64_t nodes_cap, void *tris_out, int64_t *n_nodes, int32_t *depth);
 
 /* Frees the scene's device memory.  Views of the scene must be destroyed first. */
 RPL_API void rpl_scene_destroy(rpl_scene_t scene);

@@ -136,6 +136,7 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
         pp.poses = link_poses;
         pp.link_root = si.link_root;
         pp.tnodes = si.tnodes;
+        pp.wide = si.wide;
         pp.intr = nullptr;
         pp.link_xf = reinterpret_cast<float4 *>(sb);
         pp.link_box = reinterpret_cast<float4 *>(sb + off_box);
@@ -150,6 +151,8 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
             RenderParams rp{};
             rp.tnodes = si.tnodes;
             rp.ttris = si.ttris;
+            rp.wide = si.wide;
+            rp.out_dtype = RPL_OUT_F32;
             rp.lnodes = si.lnodes;
             rp.ltris = si.ltris;
             rp.link_xf = pp.link_xf;

@@ -13,6 +13,7 @@
 // The path is pointer chasing, not a dense contraction, so it runs on the SIMT pipes: node and
 // triangle fetches are 16-byte read-only vector loads, the per-ray stack is short, rays of a warp
 // are a compact pixel tile so their fetches coalesce and hit the same cache lines.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -87,6 +88,30 @@ __device__ __forceinline__ bool boxes_overlap(float alx, float ahx, float aly, f
                                               const float blo[3], const float bhi[3]) {
     return alx <= bhi[0] && blo[0] <= ahx && aly <= bhi[1] && blo[1] <= ahy && alz <= bhi[2] && blo[2] <= ahz;
 }
+
+// Deepest binary node below `node` that holds everything inside the AABB [lo, hi]: descend while
+// exactly one child's box meets the AABB and that child is an inner node.
+__device__ __forceinline__ int descend_binary(const float4 *__restrict__ nodes, int node, const float lo[3],
+                                              const float hi[3]) {
+#pragma unroll 1
+    for (int depth = 0; depth < kStackDepth; ++depth) {
+        const float4 *n = nodes + 4 * node;
+        const float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2);
+        const int4 n3 = __ldg(reinterpret_cast<const int4 *>(n + 3));
+        const bool h0 = !(n3.x < 0 && n3.z == 0) && boxes_overlap(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, lo, hi);
+        const bool h1 = !(n3.y < 0 && n3.w == 0) && boxes_overlap(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, lo, hi);
+        int next = -1;
+        if (h0 && !h1 && n3.x >= 0) next = n3.x;
+        if (h1 && !h0 && n3.y >= 0) next = n3.y;
+        if (next < 0) break;
+        node = next;
+    }
+    return node;
+}
+
+// The same for the eight-wide layout (defined with the wide traversal below).
+__device__ __forceinline__ int descend_wide(const float4 *__restrict__ nodes, int node, const float lo[3],
+                                            const float hi[3]);
 
 __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepParams p) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -197,19 +222,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
 
     // 2) terrain entry node: descend while exactly one child's box meets the view volume's AABB and
     //    that child is an inner node; nothing in the other subtrees can be hit by this camera's rays
-    int node = 0;
-    for (int depth = 0; depth < kStackDepth; ++depth) {
-        const float4 *n = p.tnodes + 4 * node;
-        const float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2);
-        const int4 n3 = __ldg(reinterpret_cast<const int4 *>(n + 3));
-        const bool h0 = !(n3.x < 0 && n3.z == 0) && boxes_overlap(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, flo, fhi);
-        const bool h1 = !(n3.y < 0 && n3.w == 0) && boxes_overlap(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, flo, fhi);
-        int next = -1;
-        if (h0 && !h1 && n3.x >= 0) next = n3.x;
-        if (h1 && !h0 && n3.y >= 0) next = n3.y;
-        if (next < 0) break;
-        node = next;
-    }
+    const int node = p.wide ? descend_wide(p.tnodes, 0, flo, fhi) : descend_binary(p.tnodes, 0, flo, fhi);
     // 3) latency of this (env, camera, step): k = (w0 (Lmax + 1)) >> 32 from the word with pixel field
     //    0xFFFFFFFF; source step s' = max(s - k, first step since reset); stored as s - s'
     uint32_t delta = 0;
@@ -414,7 +427,165 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Eight-wide quantised BVH (layout in bvh8.h)
+// ---------------------------------------------------------------------------------------------
+// Byte j of w as a float: the byte is placed into the mantissa of 2^23 and 2^23 subtracted (exact).
+template <int j>
+__device__ __forceinline__ float qbyte(uint32_t w) {
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650 + j)) - 8388608.0f;
+}
+
+// Permutes an 8-bit slot mask into traversal order (bit i <- slot i ^ oct) and back.
+__device__ __forceinline__ uint32_t oct_permute(uint32_t m, int oct) {
+    if (oct & 1) m = ((m & 0x55u) << 1) | ((m & 0xAAu) >> 1);
+    if (oct & 2) m = ((m & 0x33u) << 2) | ((m & 0xCCu) >> 2);
+    if (oct & 4) m = ((m & 0x0Fu) << 4) | ((m & 0xF0u) >> 4);
+    return m;
+}
+
+struct WideNode {
+    uint4 a, b, c, d, f;
+};
+
+__device__ __forceinline__ WideNode load_wide(const float4 *__restrict__ nodes, int i) {
+    const uint4 *n = reinterpret_cast<const uint4 *>(nodes) + 5 * (int64_t)i;
+    return WideNode{__ldg(n), __ldg(n + 1), __ldg(n + 2), __ldg(n + 3), __ldg(n + 4)};
+}
+
+// Slab tests of the eight children of one wide node against (0, tmax]; returns the hit mask in slot
+// order.  t(q) = q * step * (1/d) + (origin - o) * (1/d) per axis, near/far planes chosen by the
+// sign of d, so an empty slot (q_lo 255, q_hi 0) never hits.
+__device__ __forceinline__ uint32_t wide_hits(const WideNode &n, const Ray &r, float tmax) {
+    const float ox = __uint_as_float(n.a.x), oy = __uint_as_float(n.a.y), oz = __uint_as_float(n.a.z);
+    const float sx = __uint_as_float((n.a.w & 0xFFu) << 23), sy = __uint_as_float(((n.a.w >> 8) & 0xFFu) << 23),
+                sz = __uint_as_float(((n.a.w >> 16) & 0xFFu) << 23);
+    const float ax = sx * r.invd.x, ay = sy * r.invd.y, az = sz * r.invd.z;
+    const float bx = fmaf(ox, r.invd.x, -r.oinv.x), by = fmaf(oy, r.invd.y, -r.oinv.y),
+                bz = fmaf(oz, r.invd.z, -r.oinv.z);
+    const bool px = r.invd.x >= 0.f, py = r.invd.y >= 0.f, pz = r.invd.z >= 0.f;
+    // words: q_lo x (c.x, c.y), y (c.z, c.w), z (d.x, d.y); q_hi x (d.z, d.w), y (f.x, f.y), z (f.z, f.w)
+    const uint32_t nx0 = px ? n.c.x : n.d.z, nx1 = px ? n.c.y : n.d.w, fx0 = px ? n.d.z : n.c.x, fx1 = px ? n.d.w : n.c.y;
+    const uint32_t ny0 = py ? n.c.z : n.f.x, ny1 = py ? n.c.w : n.f.y, fy0 = py ? n.f.x : n.c.z, fy1 = py ? n.f.y : n.c.w;
+    const uint32_t nz0 = pz ? n.d.x : n.f.z, nz1 = pz ? n.d.y : n.f.w, fz0 = pz ? n.f.z : n.d.x, fz1 = pz ? n.f.w : n.d.y;
+    uint32_t hits = 0;
+#define RPL_WIDE_SLOT(S, NX, NY, NZ, FX, FY, FZ, J)                                                          \
+    {                                                                                                      \
+        const float tin = fmaxf(fmaxf(fmaf(qbyte<J>(NX), ax, bx), fmaf(qbyte<J>(NY), ay, by)),             \
+                                fmaxf(fmaf(qbyte<J>(NZ), az, bz), 0.0f));                                  \
+        const float tout = fminf(fminf(fmaf(qbyte<J>(FX), ax, bx), fmaf(qbyte<J>(FY), ay, by)),            \
+                                 fminf(fmaf(qbyte<J>(FZ), az, bz), tmax));                                 \
+        hits |= (tin <= tout ? 1u : 0u) << (S);                                                            \
+    }
+    RPL_WIDE_SLOT(0, nx0, ny0, nz0, fx0, fy0, fz0, 0)
+    RPL_WIDE_SLOT(1, nx0, ny0, nz0, fx0, fy0, fz0, 1)
+    RPL_WIDE_SLOT(2, nx0, ny0, nz0, fx0, fy0, fz0, 2)
+    RPL_WIDE_SLOT(3, nx0, ny0, nz0, fx0, fy0, fz0, 3)
+    RPL_WIDE_SLOT(4, nx1, ny1, nz1, fx1, fy1, fz1, 0)
+    RPL_WIDE_SLOT(5, nx1, ny1, nz1, fx1, fy1, fz1, 1)
+    RPL_WIDE_SLOT(6, nx1, ny1, nz1, fx1, fy1, fz1, 2)
+    RPL_WIDE_SLOT(7, nx1, ny1, nz1, fx1, fy1, fz1, 3)
+#undef RPL_WIDE_SLOT
+    return hits;
+}
+
+__device__ __forceinline__ uint32_t meta_byte(const WideNode &n, int s) {
+    return ((s < 4 ? n.b.z : n.b.w) >> (8 * (s & 3))) & 0xFFu;
+}
+
+// Dequantised box of slot s (rounded outward by the padding of the caller's overlap test).
+__device__ __forceinline__ void wide_child_box(const WideNode &n, int s, float lo[3], float hi[3]) {
+    const uint32_t wl[3][2] = {{n.c.x, n.c.y}, {n.c.z, n.c.w}, {n.d.x, n.d.y}};
+    const uint32_t wh[3][2] = {{n.d.z, n.d.w}, {n.f.x, n.f.y}, {n.f.z, n.f.w}};
+    const uint32_t org[3] = {n.a.x, n.a.y, n.a.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float step = __uint_as_float(((n.a.w >> (8 * a)) & 0xFFu) << 23);
+        const float o = __uint_as_float(org[a]);
+        const float ql = (float)((wl[a][s >> 2] >> (8 * (s & 3))) & 0xFFu);
+        const float qh = (float)((wh[a][s >> 2] >> (8 * (s & 3))) & 0xFFu);
+        lo[a] = fmaf(ql, step, o);
+        hi[a] = fmaf(qh, step, o);
+    }
+}
+
+// Deepest wide node below `node` that holds everything inside the AABB [lo, hi]: descend while
+// exactly one slot's box meets the AABB and that slot is an inner node.
+__device__ __forceinline__ int descend_wide(const float4 *__restrict__ nodes, int node, const float lo[3],
+                                            const float hi[3]) {
+#pragma unroll 1
+    for (int depth = 0; depth < kStackDepth; ++depth) {
+        const WideNode n = load_wide(nodes, node);
+        int n_hit = 0, slot = -1;
+#pragma unroll 1
+        for (int s = 0; s < 8; ++s) {
+            if (meta_byte(n, s) == 0) continue;
+            float bl[3], bh[3];
+            wide_child_box(n, s, bl, bh);
+            if (boxes_overlap(bl[0], bh[0], bl[1], bh[1], bl[2], bh[2], lo, hi)) {
+                ++n_hit;
+                slot = s;
+            }
+        }
+        const uint32_t imask = n.a.w >> 24;
+        if (n_hit != 1 || !((imask >> slot) & 1u)) break;
+        node = (int)n.b.x + (int)(meta_byte(n, slot) & 0x7Fu);
+    }
+    return node;
+}
+
+// Closest hit in the wide terrain BVH.  The stack holds groups of inner children still to visit,
+// (first child index, imask | remaining traversal-order mask << 8); children are taken in the order
+// slot ^ octant(d), roughly front to back.  Leaf children of a node are tested when it is visited.
 template <bool kCount>
+__device__ __forceinline__ bool traverse8(const float4 *__restrict__ nodes, const float4 *__restrict__ tris, int root,
+                                          const Ray &r, int oct, float &tmax, bool &hit, Counts &cnt) {
+    uint2 stack[kStackDepth];
+    int sp = 0;
+    int node = root;
+#pragma unroll 1
+    for (;;) {
+        const WideNode n = load_wide(nodes, node);
+        if (kCount) ++cnt.nodes;
+        const uint32_t hits = wide_hits(n, r, tmax);
+        const uint32_t imask = n.a.w >> 24;
+        // leaf children, nearest first
+        uint32_t leaves = oct_permute(hits & ~imask & 0xFFu, oct);
+#pragma unroll 1
+        while (leaves) {
+            const int s = (__ffs(leaves) - 1) ^ oct;
+            leaves &= leaves - 1;
+            const uint32_t m = meta_byte(n, s);
+            leaf<true, kCount>(tris, (int)n.b.y + (int)((m >> 2) & 31u), (int)(m & 3u) + 1, r, tmax, hit, cnt);
+        }
+        uint32_t inner = oct_permute(hits & imask, oct);
+        uint32_t base = n.b.x, im = imask;
+        if (!inner) {
+            // next group from the stack
+            bool found = false;
+            while (sp > 0) {
+                const uint2 g = stack[--sp];
+                if (g.y >> 8) {
+                    base = g.x;
+                    im = g.y & 0xFFu;
+                    inner = g.y >> 8;
+                    found = true;
+                    break;
+                }
+            }
+            if (!found) return true;
+        }
+        const int s = (__ffs(inner) - 1) ^ oct;
+        inner &= inner - 1;
+        if (inner) {
+            if (sp == kStackDepth) return false;
+            stack[sp++] = make_uint2(base, im | (inner << 8));
+        }
+        node = (int)base + __popc(im & ((1u << s) - 1u));
+    }
+}
+
+template <bool kCount, bool kWide>
 __global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ RenderParams p) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -479,20 +650,8 @@ __global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ 
             thi[a] = hi + slack;
         }
     }
-    int entry = __float_as_int(CV.z);
-#pragma unroll 1
-    for (int depth = 0; depth < kStackDepth; ++depth) {
-        const float4 *n = p.tnodes + 4 * entry;
-        const float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2);
-        const int4 n3 = __ldg(reinterpret_cast<const int4 *>(n + 3));
-        const bool h0 = !(n3.x < 0 && n3.z == 0) && boxes_overlap(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tlo, thi);
-        const bool h1 = !(n3.y < 0 && n3.w == 0) && boxes_overlap(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tlo, thi);
-        int next = -1;
-        if (h0 && !h1 && n3.x >= 0) next = n3.x;
-        if (h1 && !h0 && n3.y >= 0) next = n3.y;
-        if (next < 0) break;
-        entry = next;
-    }
+    const int entry = kWide ? descend_wide(p.tnodes, __float_as_int(CV.z), tlo, thi)
+                             : descend_binary(p.tnodes, __float_as_int(CV.z), tlo, thi);
     uint64_t link_mask = 0;
 #pragma unroll 1
     for (uint64_t mk = cam_mask; mk; mk &= mk - 1) {
@@ -527,7 +686,12 @@ __global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ 
         ok &= traverse<false, kCount>(p.lnodes, p.ltris, root, lr, tmax, hit, cnt_l);
     }
     // 2) static terrain, bounded by the closest body hit
-    ok &= traverse<true, kCount>(p.tnodes, p.ttris, entry, ray, tmax, hit, cnt_t);
+    if (kWide) {
+        const int oct = (d.x < 0.f ? 1 : 0) | (d.y < 0.f ? 2 : 0) | (d.z < 0.f ? 4 : 0);
+        ok &= traverse8<kCount>(p.tnodes, p.ttris, entry, ray, oct, tmax, hit, cnt_t);
+    } else {
+        ok &= traverse<true, kCount>(p.tnodes, p.ttris, entry, ray, tmax, hit, cnt_t);
+    }
     if (!ok) atomicOr(p.err, 1);
 
     float z = hit ? fminf(m * tmax, cam.d_max) : cam.d_max;
@@ -560,7 +724,15 @@ __global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ 
     } else {
         z = fminf(fmaxf(z, cam.d_min), cam.d_max);
     }
-    p.out[(int64_t)e * p.pix_per_env + col] = z;
+    const int64_t o_idx = (int64_t)e * p.pix_per_env + col;
+    if (p.out_dtype == RPL_OUT_F32) {
+        static_cast<float *>(p.out)[o_idx] = z;
+    } else if (p.out_dtype == RPL_OUT_F16) {
+        static_cast<__half *>(p.out)[o_idx] = __float2half_rn(z);
+    } else {
+        const float q = rintf(fminf(fmaxf(z / cam.d_max, 0.f), 1.f) * 65535.f);
+        static_cast<uint16_t *>(p.out)[o_idx] = (uint16_t)q;
+    }
 
     if (kCount) {
         const unsigned mask = __activemask();
@@ -593,10 +765,17 @@ cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
     if (warps == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((warps + 3) / 4);
     (void)cudaGetLastError();
-    if (count)
-        render_kernel<true><<<blocks, 128, 0, s>>>(p);
-    else
-        render_kernel<false><<<blocks, 128, 0, s>>>(p);
+    if (p.wide) {
+        if (count)
+            render_kernel<true, true><<<blocks, 128, 0, s>>>(p);
+        else
+            render_kernel<false, true><<<blocks, 128, 0, s>>>(p);
+    } else {
+        if (count)
+            render_kernel<true, false><<<blocks, 128, 0, s>>>(p);
+        else
+            render_kernel<false, false><<<blocks, 128, 0, s>>>(p);
+    }
     return cudaGetLastError();
 }
 

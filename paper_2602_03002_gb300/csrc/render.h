@@ -27,7 +27,8 @@ struct CamDev {
 struct PrepParams {
     const float *poses;        // [E, L, 7]
     const float4 *link_root;   // [RPL_MAX_LINKS * 2] link-frame root boxes (lo, hi)
-    const float4 *tnodes;      // terrain BVH nodes
+    const float4 *tnodes;      // terrain BVH nodes (binary layout, or wide layout when wide != 0)
+    int32_t wide;              // 1: terrain nodes are 80-byte eight-wide quantised nodes (bvh8.h)
     const float *intr;         // [E, C, 4] per-env intrinsics or null
     float4 *link_xf;
     float4 *link_box;
@@ -42,8 +43,10 @@ struct PrepParams {
 };
 
 struct RenderParams {
-    const float4 *tnodes;   // terrain BVH nodes (4 float4 each), root = node 0
+    const float4 *tnodes;   // terrain BVH nodes (4 float4 each, or 5 when wide), root = node 0
     const float4 *ttris;    // terrain triangles (3 float4 each)
+    int32_t wide;           // 1: eight-wide quantised terrain BVH
+    int32_t out_dtype;      // rpl_out_dtype of `out`
     const float4 *lnodes;   // all link BVH nodes
     const float4 *ltris;    // all link triangles
     const float4 *link_xf;
@@ -63,7 +66,7 @@ struct RenderParams {
     int32_t sensor_on;
     float *ring;                    // [E, span, pix_per_env] or null when span == 1
     const int64_t *s_first;         // [E]
-    float *out;                     // [E, pix_per_env]
+    void *out;                      // [E, pix_per_env] of out_dtype
     int32_t *err;                   // error word (bit 0: traversal stack overflow)
     unsigned long long *counters;   // rpl_counters fields, or null
 };

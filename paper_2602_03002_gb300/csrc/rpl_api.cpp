@@ -14,6 +14,7 @@
 
 #include "../../include/rpl.h"
 #include "bvh.h"
+#include "bvh8.h"
 #include "render.h"
 #include "scene_access.h"
 
@@ -171,9 +172,12 @@ RPL_API rpl_status rpl_scene_create(const float *verts, int64_t n_verts, const i
     if (n_tris >= (int64_t)0x0FFFFFFF) return fail(RPL_ERR_CAPACITY, "rpl_scene_create: too many triangles");
     rpl_scene_opts o{};
     if (opts) o = *opts;
-    if (o.bvh_kind != RPL_BVH2) return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: unknown bvh_kind %d", o.bvh_kind);
+    if (o.bvh_kind != RPL_BVH2 && o.bvh_kind != RPL_BVH8Q8)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: unknown bvh_kind %d", o.bvh_kind);
     if (o.max_leaf_size < 0 || o.max_leaf_size > 8)
         return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: max_leaf_size must be 0..8");
+    if (o.bvh_kind == RPL_BVH8Q8 && o.max_leaf_size > 4)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: the wide BVH holds at most 4 triangles per leaf");
     int n_dev = 0;
     if (cudaGetDeviceCount(&n_dev) != cudaSuccess || o.device < 0 || o.device >= n_dev) {
         cudaGetLastError();
@@ -212,15 +216,31 @@ RPL_API rpl_status rpl_scene_create(const float *verts, int64_t n_verts, const i
             delete s;
             return fail(RPL_ERR_CAPACITY, "rpl_scene_create: BVH depth %d exceeds %d", bvh.depth, kStackDepth);
         }
+        const void *node_src = bvh.nodes.data();
+        size_t node_bytes = bvh.nodes.size() * sizeof(BvhNode);
+        const std::vector<BvhTri> *tri_src = &bvh.tris;
+        HostBvh8 wide;
         s->t_n_nodes = (int64_t)bvh.nodes.size();
-        s->t_n_tris = (int64_t)bvh.tris.size();
         s->t_depth = bvh.depth;
-        cudaError_t e = s->t_nodes.alloc(bvh.nodes.size() * sizeof(BvhNode));
-        if (e == cudaSuccess) e = s->t_tris.alloc(std::max<size_t>(bvh.tris.size(), 1) * sizeof(BvhTri));
-        if (e == cudaSuccess)
-            e = cudaMemcpy(s->t_nodes.p, bvh.nodes.data(), bvh.nodes.size() * sizeof(BvhNode), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && !bvh.tris.empty())
-            e = cudaMemcpy(s->t_tris.p, bvh.tris.data(), bvh.tris.size() * sizeof(BvhTri), cudaMemcpyHostToDevice);
+        if (o.bvh_kind == RPL_BVH8Q8) {
+            if (collapse_bvh8(bvh, &wide) != 0) {
+                delete s;
+                return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: a leaf holds more than 4 triangles");
+            }
+            bvh.nodes.clear();
+            bvh.nodes.shrink_to_fit();
+            node_src = wide.nodes.data();
+            node_bytes = wide.nodes.size() * sizeof(Bvh8Node);
+            tri_src = &wide.tris;
+            s->t_n_nodes = (int64_t)wide.nodes.size();
+            s->t_depth = wide.depth;
+        }
+        s->t_n_tris = (int64_t)tri_src->size();
+        cudaError_t e = s->t_nodes.alloc(node_bytes);
+        if (e == cudaSuccess) e = s->t_tris.alloc(std::max<size_t>(tri_src->size(), 1) * sizeof(BvhTri));
+        if (e == cudaSuccess) e = cudaMemcpy(s->t_nodes.p, node_src, node_bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !tri_src->empty())
+            e = cudaMemcpy(s->t_tris.p, tri_src->data(), tri_src->size() * sizeof(BvhTri), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             delete s;
             return cuda_fail(e, "rpl_scene_create: uploading the terrain BVH");
@@ -314,7 +334,8 @@ RPL_API rpl_status rpl_scene_info_get(rpl_scene_t s, rpl_scene_info *info) {
     std::lock_guard<std::mutex> lk(s->mu);
     info->terrain_tris = s->t_n_tris;
     info->terrain_nodes = s->t_n_nodes;
-    info->terrain_bytes = s->t_n_nodes * (int64_t)sizeof(BvhNode) + s->t_n_tris * (int64_t)sizeof(BvhTri);
+    info->terrain_bytes = s->t_n_nodes * (int64_t)(s->opts.bvh_kind == RPL_BVH8Q8 ? sizeof(Bvh8Node) : sizeof(BvhNode)) +
+                          s->t_n_tris * (int64_t)sizeof(BvhTri);
     info->terrain_depth = s->t_depth;
     int n = 0;
     int64_t ln = 0, lt = 0;
@@ -359,6 +380,28 @@ RPL_API rpl_status rpl_bvh_build_host(const float *verts, int64_t n_verts, const
         std::memcpy(nodes_out, b.nodes.data(), b.nodes.size() * sizeof(BvhNode));
     }
     if (tris_out && n_tris > 0) std::memcpy(tris_out, b.tris.data(), b.tris.size() * sizeof(BvhTri));
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_bvh8_build_host(const float *verts, int64_t n_verts, const int32_t *tris, int64_t n_tris,
+                                       int32_t max_leaf, int32_t threads, void *nodes_out, int64_t nodes_cap,
+                                       void *tris_out, int64_t *n_nodes, int32_t *depth) {
+    if (n_verts < 0 || n_tris < 0 || !n_nodes || !depth || (n_tris > 0 && (!verts || !tris)))
+        return fail(RPL_ERR_INVALID_ARG, "rpl_bvh8_build_host: bad argument");
+    if (max_leaf < 0 || max_leaf > 4) return fail(RPL_ERR_INVALID_ARG, "rpl_bvh8_build_host: max_leaf 0..4");
+    HostBvh b;
+    int rc = build_bvh2(verts, n_verts, tris, n_tris, max_leaf, threads, &b);
+    if (rc == -1) return fail(RPL_ERR_INVALID_ARG, "rpl_bvh8_build_host: vertex index out of range");
+    if (rc != 0) return fail(RPL_ERR_OUT_OF_MEMORY, "rpl_bvh8_build_host: host allocation");
+    HostBvh8 w;
+    if (collapse_bvh8(b, &w) != 0) return fail(RPL_ERR_INVALID_ARG, "rpl_bvh8_build_host: leaf too large");
+    *n_nodes = (int64_t)w.nodes.size();
+    *depth = w.depth;
+    if (nodes_out) {
+        if (nodes_cap < (int64_t)w.nodes.size()) return fail(RPL_ERR_CAPACITY, "rpl_bvh8_build_host: nodes_cap too small");
+        std::memcpy(nodes_out, w.nodes.data(), w.nodes.size() * sizeof(Bvh8Node));
+    }
+    if (tris_out && n_tris > 0) std::memcpy(tris_out, w.tris.data(), w.tris.size() * sizeof(BvhTri));
     return RPL_OK;
 }
 
@@ -480,7 +523,8 @@ RPL_API rpl_status rpl_sensor_set(rpl_view_t v, const rpl_sensor_params *prm) {
         return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_set: sigmas must be finite and >= 0, fill finite");
     if (prm->depth_kind != RPL_DEPTH_Z && prm->depth_kind != RPL_DEPTH_RANGE)
         return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_set: unknown depth_kind");
-    if (prm->out_dtype != RPL_OUT_F32) return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_set: unknown out_dtype");
+    if (prm->out_dtype != RPL_OUT_F32 && prm->out_dtype != RPL_OUT_F16 && prm->out_dtype != RPL_OUT_U16)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_set: unknown out_dtype");
     DeviceGuard g(v->scene->device);
     v->sensor = *prm;
     v->has_last = false;
@@ -518,7 +562,9 @@ static void fill_cams(const rpl_view *v, CamDev *out) {
     }
 }
 
-static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int64_t env_offset, float *out_dev,
+static size_t out_elem_bytes(const rpl_view *v) { return v->sensor.out_dtype == RPL_OUT_F32 ? 4 : 2; }
+
+static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int64_t env_offset, void *out_dev,
                           cudaStream_t st, bool count, unsigned long long *counters_dev) {
     rpl_scene *s = v->scene;
     cudaError_t e;
@@ -531,6 +577,7 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
     pp.poses = poses_dev;
     pp.link_root = s->l_roots.as<const float4>();
     pp.tnodes = s->t_nodes.as<const float4>();
+    pp.wide = s->opts.bvh_kind == RPL_BVH8Q8 ? 1 : 0;
     pp.intr = v->intr.p ? v->intr.as<const float>() : nullptr;
     for (int l = 0; l < RPL_MAX_LINKS; ++l) pp.lroot[l] = l < v->L ? s->l_root[l] : -1;
     pp.link_xf = v->link_xf.as<float4>();
@@ -552,6 +599,8 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
     RenderParams rp{};
     rp.tnodes = s->t_nodes.as<const float4>();
     rp.ttris = s->t_tris.as<const float4>();
+    rp.wide = pp.wide;
+    rp.out_dtype = v->sensor.out_dtype;
     rp.lnodes = s->l_nodes.as<const float4>();
     rp.ltris = s->l_tris.as<const float4>();
     rp.link_xf = v->link_xf.as<const float4>();
@@ -626,7 +675,7 @@ RPL_API rpl_status rpl_render(rpl_view_t v, const float *poses, int64_t step, in
     if (g.err != cudaSuccess) return cuda_fail(g.err, "rpl_render: cudaSetDevice");
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     const size_t pose_bytes = (size_t)v->E * v->L * 7 * sizeof(float);
-    const size_t out_bytes = (size_t)v->E * v->P * sizeof(float);
+    const size_t out_bytes = (size_t)v->E * v->P * out_elem_bytes(v);
     // While the stream is being captured into a graph the buffers must be device memory: no
     // pointer queries are issued then.
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -640,7 +689,7 @@ RPL_API rpl_status rpl_render(rpl_view_t v, const float *poses, int64_t step, in
     if (pk == PTR_OTHER_DEVICE || ok == PTR_OTHER_DEVICE)
         return fail(RPL_ERR_INVALID_ARG, "rpl_render: a buffer lives on another GPU than the scene");
     const float *pd = poses;
-    float *od = reinterpret_cast<float *>(out);
+    void *od = out;
     cudaError_t e;
     if (pk == PTR_HOST) {
         if (v->pose_stage.bytes < pose_bytes) {
@@ -656,7 +705,7 @@ RPL_API rpl_status rpl_render(rpl_view_t v, const float *poses, int64_t step, in
             e = v->out_stage.alloc(out_bytes);
             if (e != cudaSuccess) return cuda_fail(e, "rpl_render: allocating the output staging buffer");
         }
-        od = v->out_stage.as<float>();
+        od = v->out_stage.p;
     }
     st = enqueue(v, pd, step, env_offset, od, cs, false, nullptr);
     if (st != RPL_OK) return st;
@@ -686,7 +735,7 @@ RPL_API rpl_status rpl_render_counters(rpl_view_t v, const float *poses, int64_t
     cudaError_t e = cnt.alloc(6 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt.p, 0, 6 * sizeof(unsigned long long), cs);
     if (e != cudaSuccess) return cuda_fail(e, "rpl_render_counters: counter buffer");
-    st = enqueue(v, poses, step, env_offset, reinterpret_cast<float *>(out), cs, true, cnt.as<unsigned long long>());
+    st = enqueue(v, poses, step, env_offset, out, cs, true, cnt.as<unsigned long long>());
     if (st != RPL_OK) return st;
     unsigned long long h[6];
     e = cudaMemcpyAsync(h, cnt.p, sizeof h, cudaMemcpyDeviceToHost, cs);
@@ -794,6 +843,7 @@ bool scene_inputs(const rpl_scene *s, SceneInputs *out) {
     std::lock_guard<std::mutex> lk(const_cast<rpl_scene *>(s)->mu);
     if (!s->frozen) return false;
     out->device = s->device;
+    out->wide = s->opts.bvh_kind == RPL_BVH8Q8 ? 1 : 0;
     out->tnodes = s->t_nodes.as<const float4>();
     out->ttris = s->t_tris.as<const float4>();
     out->lnodes = s->l_nodes.as<const float4>();

@@ -9,6 +9,7 @@ namespace rpl {
 
 struct SceneInputs {
     int device;
+    int wide;   // 1: the terrain BVH uses the eight-wide quantised layout
     const float4 *tnodes, *ttris, *lnodes, *ltris, *link_root;
     int32_t lroot[RPL_MAX_LINKS];
 };

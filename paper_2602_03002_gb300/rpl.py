@@ -22,6 +22,8 @@ _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "NOT_FOU
 RPL_MAX_CAMERAS = 8
 RPL_MAX_LINKS = 64
 RPL_DEPTH_Z, RPL_DEPTH_RANGE = 0, 1
+RPL_BVH2, RPL_BVH8Q8 = 0, 1
+RPL_OUT_F32, RPL_OUT_F16, RPL_OUT_U16 = 0, 1, 2
 
 
 class RplError(RuntimeError):
@@ -60,7 +62,7 @@ class rpl_counters(ctypes.Structure):
                                                 "link_nodes", "link_tris")]
 
 
-EXPORTS = ["rpl_bvh_build_host", "rpl_scene_create", "rpl_link_mesh_add", "rpl_scene_info_get", "rpl_scene_destroy", "rpl_view_create",
+EXPORTS = ["rpl_bvh_build_host", "rpl_bvh8_build_host", "rpl_scene_create", "rpl_link_mesh_add", "rpl_scene_info_get", "rpl_scene_destroy", "rpl_view_create",
            "rpl_cameras_set", "rpl_sensor_set", "rpl_view_layout", "rpl_render", "rpl_view_reset", "rpl_sync",
            "rpl_render_counters", "rpl_view_timing", "rpl_view_kernel_ms", "rpl_view_destroy", "rpl_last_error",
            "rpl_version", "rpl_render_static_scratch"]
@@ -79,6 +81,7 @@ def lib() -> ctypes.CDLL:
     P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     sig = {
         "rpl_bvh_build_host": ([P, I64, P, I64, I32, I32, P, I64, P, P, P], I32),
+        "rpl_bvh8_build_host": ([P, I64, P, I64, I32, I32, P, I64, P, P, P], I32),
         "rpl_scene_create": ([P, I64, P, I64, P, P], I32),
         "rpl_link_mesh_add": ([P, I32, P, I64, P, I64], I32),
         "rpl_scene_info_get": ([P, P], I32),
@@ -153,11 +156,26 @@ def rpl_bvh_build_host(verts, tris, max_leaf: int = 0, threads: int = 0):
     return nodes, out_t, d.value
 
 
+def rpl_bvh8_build_host(verts, tris, max_leaf: int = 0, threads: int = 0):
+    """Host eight-wide quantised BVH build (no GPU): returns (nodes [N, 20] uint32, leaf-ordered tris, depth)."""
+    v = np.ascontiguousarray(verts, np.float32).reshape(-1, 3)
+    t = np.ascontiguousarray(tris, np.int32).reshape(-1, 3)
+    n = ctypes.c_int64()
+    d = ctypes.c_int32()
+    _check(lib().rpl_bvh8_build_host(_ptr(v), len(v), _ptr(t), len(t), max_leaf, threads, None, 0, None,
+                                     ctypes.byref(n), ctypes.byref(d)))
+    nodes = np.zeros((n.value, 20), np.uint32)
+    out_t = np.zeros(len(t), TRI_DTYPE)
+    _check(lib().rpl_bvh8_build_host(_ptr(v), len(v), _ptr(t), len(t), max_leaf, threads, _ptr(nodes), n.value,
+                                     _ptr(out_t) if len(t) else None, ctypes.byref(n), ctypes.byref(d)))
+    return nodes, out_t, d.value
+
+
 def rpl_scene_create(verts, tris, device: int = 0, max_leaf_size: int = 0, build_threads: int = 0,
-                     sah_node_cost: float = 0.0) -> int:
+                     sah_node_cost: float = 0.0, bvh_kind: int = 0) -> int:
     v = np.ascontiguousarray(verts, np.float32).reshape(-1, 3) if isinstance(verts, np.ndarray) else verts
     t = np.ascontiguousarray(tris, np.int32).reshape(-1, 3) if isinstance(tris, np.ndarray) else tris
-    opts = rpl_scene_opts(device, 0, max_leaf_size, build_threads, sah_node_cost)
+    opts = rpl_scene_opts(device, bvh_kind, max_leaf_size, build_threads, sah_node_cost)
     h = ctypes.c_void_p()
     _check(lib().rpl_scene_create(_ptr(v), int(v.shape[0]), _ptr(t), int(t.shape[0]), ctypes.byref(opts),
                                   ctypes.byref(h)))
@@ -273,9 +291,10 @@ class Scene:
     """Terrain BVH (built once) plus link BVHs in their own frames."""
 
     def __init__(self, terrain_verts, terrain_tris, device: int = 0, max_leaf_size: int = 0, build_threads: int = 0,
-                 sah_node_cost: float = 0.0):
+                 sah_node_cost: float = 0.0, bvh_kind: int = 0):
         self.device = device
-        self.h = rpl_scene_create(terrain_verts, terrain_tris, device, max_leaf_size, build_threads, sah_node_cost)
+        self.h = rpl_scene_create(terrain_verts, terrain_tris, device, max_leaf_size, build_threads, sah_node_cost,
+                                  bvh_kind)
 
     @classmethod
     def from_workload(cls, w, device: int = 0, **kw) -> "Scene":
@@ -310,6 +329,7 @@ class View:
         self.n_envs, self.n_links = n_envs, n_links
         self.h = rpl_view_create(scene.h, n_envs, n_links)
         self.cams = []
+        self.out_dtype = RPL_OUT_F32
 
     @classmethod
     def from_workload(cls, scene: Scene, w, n_envs: Optional[int] = None) -> "View":
@@ -324,6 +344,7 @@ class View:
 
     def set_sensor(self, sensor):
         rpl_sensor_set(self.h, sensor)
+        self.out_dtype = int(sensor.get("out_dtype", 0) if isinstance(sensor, dict) else getattr(sensor, "out_dtype", 0))
 
     def layout(self):
         return rpl_view_layout(self.h, len(self.cams))
@@ -332,7 +353,8 @@ class View:
         import torch
         _, total = self.layout()
         dev = torch.device("cuda", self.scene.device) if device is None else device
-        return torch.empty((self.n_envs, total), dtype=torch.float32, device=dev)
+        dt = {RPL_OUT_F32: torch.float32, RPL_OUT_F16: torch.float16, RPL_OUT_U16: torch.uint16}[self.out_dtype]
+        return torch.empty((self.n_envs, total), dtype=dt, device=dev)
 
     def render(self, poses, step: int, env_offset: int = 0, out=None, stream=None):
         if out is None:

@@ -58,6 +58,7 @@ class Sensor:
     max_latency: int = 0
     seed: Tuple[int, int] = (0, 0)
     depth_kind: int = 0  # 0 = z-depth along the optical axis, 1 = range along the ray
+    out_dtype: int = 0   # 0 = float32, 1 = float16, 2 = unorm16 over [0, d_max]
 
     @property
     def enabled(self) -> bool:
