@@ -1,13 +1,19 @@
 #!/usr/bin/env python3
-"""Benchmark: multi-depth ray casting + sensor model at 4096 envs x 2 cameras x 64x48 px.
+"""Benchmark of multi-depth ray casting + sensor model (Sec. 3.2.1, Algorithm 1, Appendix A.2).
 
-One step = one call of the C ABI's rpl_render (per-env link/camera transforms, then the fused
-ray-cast + sensor kernel) over all envs with the next pose set; inputs are resident in HBM.
-Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead on a bounded
-sample of the same workload.
+Variants (``--variant``):
+  plain      4096 envs x 2 cameras x 64x48 px, 20.48M-triangle terrain, 30 links of 512 triangles,
+             sensor on (0.01 m noise, 2 % dropout, latency 0-3), binary BVH, FP32 depth (default);
+  precision  the same with the eight-wide BVH of 8-bit quantised boxes and FP16 depth;
+  batching   4096 envs x 4 uneven cameras (80x60, 80x60, 48x36, 48x36) in one launch, replayed as a
+             CUDA graph of the whole path.
+One step = the whole path over all envs with the next resident pose set: rpl_render (prep + render
+kernels), or one graph replay for ``batching``.  The launch shape is chosen by the library's
+autotuner before timing.  Rank 0 prints one JSON line.  ``--impl reference`` times the FP64 CPU
+oracle instead on a bounded sample of the same workload.
 
-Multi-GPU (torchrun): each rank renders its own 4096 envs (env_offset = rank * 4096), no data-path
-collective; the barrier and the max-over-ranks time only bracket the timed region.
+Multi-GPU (torchrun): each rank renders its own 4096 envs (env_offset = rank * envs) with no
+data-path collective; the barrier and the max-over-ranks time only bracket the timed region.
 """
 from __future__ import annotations
 
@@ -29,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Grays/s and depth frames/s at 4096 envs; serve p50/p99 latency vs plain FP32"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "render_kernel_traffic.json")
-NODE_BYTES, TRI_BYTES, BOX_BYTES = 64, 48, 32
+TRI_BYTES, BOX_BYTES = 48, 32
 
 
 def parse():
@@ -38,9 +44,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default="plain", choices=["plain", "precision", "batching"])
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--tiles", type=int, default=20)
     ap.add_argument("--pose-sets", type=int, default=8)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the oracle sample")
@@ -53,16 +61,24 @@ def dist_info():
 
 def workload(args, rank):
     from paper_2602_03002_gb300 import workloads as W
-    return W.config_scale(n_steps=args.pose_sets, n_envs=args.envs, tiles=args.tiles, seed=rank)
+    if args.variant == "batching":
+        return W.config_uneven(n_steps=args.pose_sets, n_envs=args.envs, tiles=args.tiles, seed=rank)
+    w = W.config_scale(n_steps=args.pose_sets, n_envs=args.envs, tiles=args.tiles, seed=rank)
+    if args.variant == "precision":
+        w.sensor.out_dtype = 1
+    return w
 
 
-def workload_name(w):
-    return ("plain FP32 at scale: %d envs x %d cams x %dx%d px; terrain %d tris (%dx%d tiles of 8x8 m at "
-            "0.05 m: stairs 0.22/0.25/0.30 m run, 20 deg slopes, stepping stones); %d links x %d-tri meshes; "
-            "sensor sigma %.2f m, %.0f%% dropout, latency 0-%d steps"
-            % (w.n_envs, len(w.cameras), w.cameras[0].width, w.cameras[0].height, len(w.terrain_tris),
-               int(round(np.sqrt(len(w.terrain_tris) / 51200))), int(round(np.sqrt(len(w.terrain_tris) / 51200))),
-               w.n_links, len(w.link_tris[0]), w.sensor.sigma_abs, 100 * w.sensor.p_drop, w.sensor.max_latency))
+def workload_name(w, variant):
+    cams = " + ".join("%dx%d" % (c.width, c.height) for c in w.cameras)
+    s = w.sensor
+    sensor = ("sensor sigma %.2f m, %.0f%% dropout, latency 0-%d steps" % (s.sigma_abs, 100 * s.p_drop, s.max_latency)
+              if s.enabled else "no sensor model")
+    form = {"plain": "binary BVH, FP32 depth", "precision": "8-wide BVH with 8-bit quantised boxes, FP16 depth",
+            "batching": "binary BVH, FP32 depth, one CUDA-graph replay per step"}[variant]
+    return ("%s: %d envs x cams (%s px); terrain %d tris (tiles of 8x8 m at 0.05 m: stairs 0.22/0.25/0.30 m run, "
+            "20 deg slopes, stepping stones); %d links x %d-tri meshes; %s; %s"
+            % (variant, w.n_envs, cams, len(w.terrain_tris), w.n_links, len(w.link_tris[0]), sensor, form))
 
 
 def peaks():
@@ -82,12 +98,12 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(rays):
+def traffic_per_launch(rays, variant):
     """DRAM bytes per launch from the committed ncu capture, scaled by rays; None if the kernel changed."""
     try:
         with open(TRAFFIC) as f:
             t = json.load(f)
-        if t.get("kernel_sha") != kernel_hash():
+        if t.get("kernel_sha") != kernel_hash() or t.get("variant", "plain") != variant:
             return None
         return float(t["dram_bytes"]) * rays / float(t["rays"])
     except Exception:
@@ -135,30 +151,48 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(w, seconds, rank):
-    """The FP64 oracle, as it stands, on a bounded sample of rays of the same workload."""
+def sample_rays(w, n, rng):
+    c = rng.integers(0, len(w.cameras), n)
+    wd = np.array([cam.width for cam in w.cameras])[c]
+    ht = np.array([cam.height for cam in w.cameras])[c]
+    x = (rng.random(n) * wd).astype(np.int64)
+    y = (rng.random(n) * ht).astype(np.int64)
+    return np.stack([rng.integers(0, w.n_envs, n), c, x, y], 1).astype(np.int64)
+
+
+def cpu_baseline(w, seconds, gpu_step0=None):
+    """The FP64 oracle, as it stands, on a bounded sample of rays of step 0 of the same workload.  When
+    the GPU's step-0 frame is given, the sample also yields the GPU's error against the oracle."""
     import oracle
     cores = os.cpu_count() or 1
     sc = oracle.OracleScene.from_workload(w)
     rng = np.random.default_rng(1234)
-
-    def sample(n):
-        e = rng.integers(0, w.n_envs, n)
-        c = rng.integers(0, len(w.cameras), n)
-        x = rng.integers(0, w.cameras[0].width, n)
-        y = rng.integers(0, w.cameras[0].height, n)
-        return np.stack([e, c, x, y], 1)
-
     t = time.perf_counter()
-    sc.render(w.cameras, w.poses, 0, sample(cores), w.sensor, flags=False, threads=cores)
+    sc.render(w.cameras, w.poses, 0, sample_rays(w, cores, rng), w.sensor, flags=False, threads=cores)
     probe = time.perf_counter() - t
     n = max(cores, int(cores * seconds / max(probe, 1e-3)))
-    rays = sample(n)
+    rays = sample_rays(w, n, rng)
     t = time.perf_counter()
-    sc.render(w.cameras, w.poses, 0, rays, w.sensor, flags=False, threads=cores)
+    ref = sc.render(w.cameras, w.poses, 0, rays, w.sensor, flags=False, threads=cores)
     dt = time.perf_counter() - t
     sc.close()
-    return n, dt, cores
+    out = {"value": n / dt / 1e9, "unit": "Grays/s", "cores": cores, "kind": "oracle",
+           "sample": "%d rays drawn uniformly over (env, camera, pixel) of step 0, FP64 brute force over all "
+                     "triangles, %.1f s" % (n, dt)}
+    if gpu_step0 is not None:
+        offs = w.cam_offsets()
+        cw = np.array([c.width for c in w.cameras])
+        got = gpu_step0[rays[:, 0], offs[rays[:, 1]] + rays[:, 3] * cw[rays[:, 1]] + rays[:, 2]]
+        if w.sensor.out_dtype == 2:
+            got = got * (w.cameras[0].d_max / 65535.0)
+        err = np.abs(got.astype(np.float64) - ref["depth"])
+        allow = 1e-4 + (np.spacing(np.abs(ref["depth"]).astype(np.float16)).astype(np.float64) / 2
+                        if w.sensor.out_dtype == 1 else 0.0)
+        out["error_vs_oracle"] = {"rays": int(n), "max_abs_m": float(err.max()),
+                                  "p99_abs_m": float(np.quantile(err, 0.99)), "mean_abs_m": float(err.mean()),
+                                  "mismatch_frac": float(np.mean(err > allow)),
+                                  "allowance_m": "1e-4" + (" + half an FP16 ulp" if w.sensor.out_dtype == 1 else "")}
+    return n, dt, cores, out
 
 
 def run_reference(args):
@@ -166,12 +200,11 @@ def run_reference(args):
     if rank != 0:
         return
     w = workload(args, 0)
-    vals = []
     n_tot = dt_tot = 0
+    cores = os.cpu_count() or 1
     for k in range(args.warmup + args.steps):
-        n, dt, cores = cpu_baseline(w, max(1.0, args.cpu_seconds / max(1, args.steps)), 0)
+        n, dt, cores, _ = cpu_baseline(w, max(1.0, args.cpu_seconds / max(1, args.steps)))
         if k >= args.warmup:
-            vals.append(n / dt)
             n_tot += n
             dt_tot += dt
     rate = n_tot / dt_tot
@@ -180,8 +213,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": rate / 1e9, "unit": "Grays/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt_tot / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_name(w)},
-            "frames_per_s": rate / w.cameras[0].width / w.cameras[0].height,
+            "data": "synthetic", "config": {"workload": workload_name(w, args.variant)},
+            "frames_per_s": rate / (w.pixels_per_env / len(w.cameras)),
             "e2e": {"value": rate / 1e9, "unit": "Grays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "cpu_baseline": {"value": rate / 1e9, "unit": "Grays/s", "cores": cores, "kind": "oracle",
                              "sample": sample}}
@@ -203,33 +236,53 @@ def run_ours(args):
         torch.distributed.barrier()
     w = workload(args, rank)
     env_offset = rank * args.envs
+    kind = rpl.RPL_BVH8Q8 if args.variant == "precision" else rpl.RPL_BVH2
     t0 = time.perf_counter()
-    scene = rpl.Scene.from_workload(w, device=dev)
+    scene = rpl.Scene(w.terrain_verts, w.terrain_tris, device=dev, bvh_kind=kind)
+    for l, (v_, t_) in enumerate(zip(w.link_verts, w.link_tris)):
+        scene.add_link(l, v_, t_)
     build_s = time.perf_counter() - t0
     view = rpl.View.from_workload(scene, w)
     info = scene.info()
     stream = torch.cuda.Stream(dev)
     poses = torch.from_numpy(w.poses).to(f"cuda:{dev}")
-    _, P = view.layout()
-    out = torch.empty((w.n_envs, P), dtype=torch.float32, device=f"cuda:{dev}")
+    out = view.out_tensor(torch.device("cuda", dev))
     rays = w.rays_per_step
+    graph = args.variant == "batching"
 
-    # traversal counters (untimed): algorithmic fetch bytes per ray for the roofline
+    # traversal counters (untimed, step 0): algorithmic fetch bytes per ray for the roofline
     with torch.cuda.stream(stream):
         cnt = view.render_counters(poses[0], 0, env_offset, out, stream)
-    b_nodes = (cnt["terrain_nodes"] + cnt["link_nodes"]) * NODE_BYTES
+    stream.synchronize()
+    gpu_step0 = out.float().cpu().numpy() if out.dtype != torch.uint16 else out.cpu().numpy().astype(np.float32)
+    node_bytes = 80 if kind == rpl.RPL_BVH8Q8 else 64
+    b_nodes = cnt["terrain_nodes"] * node_bytes + cnt["link_nodes"] * 64
     b_tris = (cnt["terrain_tris"] + cnt["link_tris"]) * TRI_BYTES
     b_boxes = cnt["link_boxes"] * BOX_BYTES
     # compulsory per-ray traffic: output store, ring write and (k > 0) ring read
-    b_io = rays * (4 + (8 if w.sensor.max_latency > 0 else 0))
+    out_b = out.element_size()
+    b_io = rays * (out_b + (8 if w.sensor.max_latency > 0 else 0))
     alg_bytes = b_nodes + b_tris + b_boxes + b_io
 
+    tuning, tune_ms = rpl.rpl_view_tuning_get(view.h), None
+    if not args.no_autotune:
+        with torch.cuda.stream(stream):
+            tuning, tune_ms = rpl.rpl_view_autotune(view.h, poses[0], 0, env_offset, out, stream, 3)
     view.reset(None, 0)
-    step = 0
     S = poses.shape[0]
+    pose_buf = poses[0].clone()
+    step = 0
+
+    def one_step(s):
+        if graph:
+            pose_buf.copy_(poses[s % S])
+            rpl.rpl_render_graph(view.h, pose_buf, env_offset, out, stream)
+        else:
+            rpl.rpl_render(view.h, poses[s % S], s, env_offset, out, stream)
+
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            rpl.rpl_render(view.h, poses[step % S], step, env_offset, out, stream)
+            one_step(step)
             step += 1
     stream.synchronize()
     rpl.rpl_view_timing(view.h, True)
@@ -241,7 +294,7 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         start.record(stream)
         for _ in range(args.steps):
-            rpl.rpl_render(view.h, poses[step % S], step, env_offset, out, stream)
+            one_step(step)
             step += 1
         end.record(stream)
     stream.synchronize()
@@ -263,7 +316,7 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         hp = [torch.from_numpy(w.poses[s]).pin_memory() for s in range(S)]
-        ho = torch.empty((w.n_envs, P), dtype=torch.float32).pin_memory()
+        ho = torch.empty(tuple(out.shape), dtype=out.dtype).pin_memory()
         for _ in range(2):
             rpl.rpl_render(view.h, hp[step % S], step, env_offset, ho, stream)
             step += 1
@@ -280,7 +333,7 @@ def run_ours(args):
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             e2e_s = float(tt.item())
         e2e = {"value": world * rays / e2e_s / 1e9, "unit": "Grays/s",
-               "h2d_bytes_per_step": int(hp[0].numel() * 4), "d2h_bytes_per_step": int(ho.numel() * 4),
+               "h2d_bytes_per_step": int(hp[0].numel() * 4), "d2h_bytes_per_step": int(ho.numel() * ho.element_size()),
                "ms_per_step": 1e3 * e2e_s}
 
     if rank != 0:
@@ -291,35 +344,36 @@ def run_ours(args):
     k_avg_s = statistics.mean(kms) / 1e3 if kms else ms_step / 1e3
     peak, peak_src = peaks()
     achieved = alg_bytes / k_avg_s / 1e9
-    traffic = traffic_per_launch(rays)
     line = {
         "metric": METRIC, "value": value, "unit": "Grays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(w), "envs_per_gpu": w.n_envs, "cameras": len(w.cameras),
-                   "rays_per_step_per_gpu": rays, "pose_sets": S,
+        "vs_baseline": None, "dtype": {0: "f32", 1: "f32 (f16 output)", 2: "f32 (unorm16 output)"}[w.sensor.out_dtype],
+        "data": "synthetic", "variant": args.variant,
+        "config": {"workload": workload_name(w, args.variant), "envs_per_gpu": w.n_envs, "cameras": len(w.cameras),
+                   "rays_per_step_per_gpu": rays, "pose_sets": S, "tuning": tuning,
+                   "autotune_best_ms": tune_ms,
                    "l2": "inputs larger than L2: terrain BVH %.2f GB resident, new poses each step"
                          % (info["terrain_bytes"] / 1e9)},
         "frames_per_s": frames,
         "env_steps_per_s": world * w.n_envs / (ms_step / 1e3),
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (3 if graph else 2) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
+                     "frac": achieved / peak, "traffic": traffic_per_launch(rays, args.variant),
                      "kernel": "render_kernel", "kernel_ms": 1e3 * k_avg_s,
+                     "kernel_ms_source": "CUDA events around each render launch" if kms else
+                                         "whole graph replay (events cannot be recorded inside the graph)",
                      "alg_bytes_per_ray": alg_bytes / rays, "peak_source": peak_src + " hbm_gbs",
-                     "per_ray": {"terrain_nodes": cnt["terrain_nodes"] / rays, "terrain_tris": cnt["terrain_tris"] / rays,
-                                 "link_boxes": cnt["link_boxes"] / rays, "link_nodes": cnt["link_nodes"] / rays,
-                                 "link_tris": cnt["link_tris"] / rays}},
+                     "per_ray": {k: cnt[k] / rays for k in ("terrain_nodes", "terrain_tris", "link_boxes",
+                                                            "link_nodes", "link_tris")}},
         "clocks": ck,
         "e2e": e2e,
         "scene": {"terrain_tris": info["terrain_tris"], "terrain_nodes": info["terrain_nodes"],
-                  "terrain_depth": info["terrain_depth"], "bvh_build_s": build_s},
+                  "terrain_depth": info["terrain_depth"], "terrain_bytes": info["terrain_bytes"],
+                  "bvh_build_s": build_s},
     }
     if world == 1 and not args.no_cpu_baseline:
-        n, dt, cores = cpu_baseline(w, args.cpu_seconds, rank)
-        line["cpu_baseline"] = {"value": n / dt / 1e9, "unit": "Grays/s", "cores": cores, "kind": "oracle",
-                                "sample": "%d rays drawn uniformly over (env, camera, pixel) of step 0, FP64 "
-                                          "brute force over all triangles, %.1f s" % (n, dt)}
+        _, _, _, cb = cpu_baseline(w, args.cpu_seconds, gpu_step0)
+        line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

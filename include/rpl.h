@@ -215,6 +215,43 @@ RPL_API rpl_status rpl_view_layout(rpl_view_t view, int64_t *cam_offsets, int64_
 RPL_API rpl_status rpl_render(rpl_view_t view, const float *link_poses, int64_t step,
                               int64_t env_offset, void *depth_out, void *stream);
 
+/* Launch shape of the render kernel.  tile_w x tile_h = 32 rays per warp (4x8, 8x4 or 16x2
+ * pixels of one camera); persistent: launch only as many blocks as fit on the GPU at once and let
+ * warps stride over the tiles; terrain_first: query the terrain before the links (Alg. 1 queries
+ * the bodies first; the depth is the same either way); min_blocks: 8 (up to 64 registers per
+ * thread) or 12 (up to 40) resident blocks of 128 threads per SM.  The shape never changes the
+ * result, only the speed.  Default: 8x4, not persistent, links first, 8. */
+typedef struct {
+    int32_t tile_w, tile_h;
+    int32_t persistent;
+    int32_t terrain_first;
+    int32_t min_blocks;
+} rpl_tuning;
+
+RPL_API rpl_status rpl_view_tuning_set(rpl_view_t view, const rpl_tuning *tuning);
+RPL_API rpl_status rpl_view_tuning_get(rpl_view_t view, rpl_tuning *tuning);
+
+/* Autotuner: renders `step` (same step rules as rpl_render; device buffers only) `reps` times
+ * with each of the 24 launch shapes (tile 8x4 / 4x8 / 16x2, persistent or not, links or terrain
+ * first, 8 or 12 blocks per SM), times them with CUDA events on `stream`, keeps the fastest on the
+ * view and returns it with its mean time per render.  Synchronises; for setup, not the hot loop. */
+RPL_API rpl_status rpl_view_autotune(rpl_view_t view, const float *link_poses, int64_t step,
+                                     int64_t env_offset, void *depth_out, void *stream, int32_t reps,
+                                     rpl_tuning *best, float *best_ms);
+
+/* Render the next step by replaying a CUDA graph of the whole path (Sec. 3.2.1: the pipeline is
+ * captured into a CUDA graph for low-overhead replay).  The first call, and any call after the
+ * buffers, env_offset, cameras, sensor or tuning changed, captures prep + render + a step-advance
+ * kernel into a graph (on a view-owned stream) and instantiates it; every call then launches it on
+ * `stream`.  The kernels read the step from a view-owned device counter that the graph advances,
+ * so replays continue the sensor history: the step rendered is the previous step + 1 (0 for a new
+ * view, or the step given to a full rpl_view_reset) and is returned in *step_out (may be NULL).
+ * link_poses and depth_out must be device memory; their contents are read/written at replay
+ * time.  Mixing with rpl_render is allowed (the counter is resynchronised with a tiny kernel).
+ * Errors: INVALID_ARG, CUDA, DEVICE_FAULT. */
+RPL_API rpl_status rpl_render_graph(rpl_view_t view, const float *link_poses, int64_t env_offset,
+                                    void *depth_out, void *stream, int64_t *step_out);
+
 /* Restart the sensor history at `step` for the envs whose byte in env_mask (host or device,
  * [n_envs] uint8) is non-zero, or for all envs when env_mask is NULL: from then on the source step
  * of those envs is never older than `step`.  With a mask, `step` must be the next step to render

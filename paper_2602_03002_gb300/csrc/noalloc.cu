@@ -183,6 +183,8 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
             rp.out = depth_out;
             rp.err = reinterpret_cast<int32_t *>(sb + off_err);
             rp.counters = nullptr;
+            rp.tile_w_log2 = 3;   // 8x4 tiles, as counted above
+            rp.min_blocks = 8;
             e = launch_render(rp, false, cs);
         }
         if (e != cudaSuccess) st = set_error(RPL_ERR_CUDA, cudaGetErrorString(e));

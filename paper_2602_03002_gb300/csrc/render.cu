@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <algorithm>
 #include <climits>
 
 #include "render.h"
@@ -227,12 +228,13 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
     //    0xFFFFFFFF; source step s' = max(s - k, first step since reset); stored as s - s'
     uint32_t delta = 0;
     if (p.span > 1) {
-        const uint4 wl = sensor_words(p.env_offset + (uint32_t)e, (uint32_t)c, 0xFFFFFFFFu, p.step, p.seed0, p.seed1);
-        int64_t src = p.step - (int64_t)__umulhi(wl.x, p.span);
+        const int64_t step = p.step_dev ? *p.step_dev : p.step;
+        const uint4 wl = sensor_words(p.env_offset + (uint32_t)e, (uint32_t)c, 0xFFFFFFFFu, step, p.seed0, p.seed1);
+        int64_t src = step - (int64_t)__umulhi(wl.x, p.span);
         const int64_t first = p.s_first[e];
         if (src < first) src = first;
-        if (src > p.step) src = p.step;
-        delta = (uint32_t)(p.step - src);
+        if (src > step) src = step;
+        delta = (uint32_t)(step - src);
     }
     p.cam_xf[5 * j + 4] = make_float4(__uint_as_float((uint32_t)mask), __uint_as_float((uint32_t)(mask >> 32)),
                                       __int_as_float(node), __uint_as_float(delta));
@@ -585,19 +587,20 @@ __device__ __forceinline__ bool traverse8(const float4 *__restrict__ nodes, cons
     }
 }
 
+// One warp renders one tile of 32 pixel rays (tile_w x tile_h, tile_w = 2^tile_w_log2) of one
+// (env, camera).  Called once per warp, or in a grid-stride loop by the persistent launch; `warp` is
+// uniform across the warp so the warp-wide reductions below see all 32 lanes.
 template <bool kCount, bool kWide>
-__global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ RenderParams p) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (warp >= (int64_t)p.E * p.tiles_per_env) return;
+__device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp, int lane, int64_t step) {
     const int e = (int)(warp / p.tiles_per_env);
     const int r_tile = (int)(warp - (int64_t)e * p.tiles_per_env);
     int c = 0;
     while (c + 1 < p.C && r_tile >= p.cams[c + 1].tile_off) ++c;
     const CamDev &cam = p.cams[c];
     const int t = r_tile - cam.tile_off;
-    const int x = (t % cam.tiles_x) * 8 + (lane & 7);
-    const int y = (t / cam.tiles_x) * 4 + (lane >> 3);
+    const int tw_log2 = p.tile_w_log2, th = 32 >> tw_log2;
+    const int x = (t % cam.tiles_x) * (1 << tw_log2) + (lane & ((1 << tw_log2) - 1));
+    const int y = (t / cam.tiles_x) * th + (lane >> tw_log2);
     // lanes outside a ragged tile still take part in the warp-wide reductions below
     const bool active = x < cam.width && y < cam.height;
     const int xs = min(x, cam.width - 1), ys = min(y, cam.height - 1);
@@ -662,8 +665,11 @@ __global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ 
     }
     if (!active) return;
 
+    // Both queries shrink the shared bound tmax; the minimum does not depend on their order
+    // (Alg. 1 queries the bodies first; terrain first makes the link queries shorter instead).
     // 1) dynamic robot bodies that the tile can reach: rays move into each link frame
     //    (o_b = R^T (o - t), d_b = R^T d)
+    auto query_links = [&]() {
 #pragma unroll 1
     for (uint64_t mk = link_mask; mk; mk &= mk - 1) {
         const int l = __ffsll((long long)mk) - 1;
@@ -685,12 +691,22 @@ __global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ 
         make_ray(lr, ob, make_float3(0.f, 0.f, 0.f), db);
         ok &= traverse<false, kCount>(p.lnodes, p.ltris, root, lr, tmax, hit, cnt_l);
     }
-    // 2) static terrain, bounded by the closest body hit
-    if (kWide) {
-        const int oct = (d.x < 0.f ? 1 : 0) | (d.y < 0.f ? 2 : 0) | (d.z < 0.f ? 4 : 0);
-        ok &= traverse8<kCount>(p.tnodes, p.ttris, entry, ray, oct, tmax, hit, cnt_t);
+    };
+    // 2) static terrain, bounded by the closest hit so far
+    auto query_terrain = [&]() {
+        if (kWide) {
+            const int oct = (d.x < 0.f ? 1 : 0) | (d.y < 0.f ? 2 : 0) | (d.z < 0.f ? 4 : 0);
+            ok &= traverse8<kCount>(p.tnodes, p.ttris, entry, ray, oct, tmax, hit, cnt_t);
+        } else {
+            ok &= traverse<true, kCount>(p.tnodes, p.ttris, entry, ray, tmax, hit, cnt_t);
+        }
+    };
+    if (p.terrain_first) {
+        query_terrain();
+        query_links();
     } else {
-        ok &= traverse<true, kCount>(p.tnodes, p.ttris, entry, ray, tmax, hit, cnt_t);
+        query_links();
+        query_terrain();
     }
     if (!ok) atomicOr(p.err, 1);
 
@@ -698,7 +714,6 @@ __global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ 
     const uint32_t pix = (uint32_t)(y * cam.width + x);
     const int64_t col = (int64_t)cam.pix_off + pix;
     if (p.sensor_on) {
-        const int64_t step = p.step;
         const int64_t span = p.span;
         const uint32_t ge = p.env_offset + (uint32_t)e;
         int64_t src = step;
@@ -745,6 +760,23 @@ __global__ void __launch_bounds__(128, 8) render_kernel(const __grid_constant__ 
     }
 }
 
+// kMinBlocks caps registers so that many blocks of 128 threads stay resident per SM (8 -> 64
+// registers, 12 -> 40).  With p.persistent the grid holds only as many blocks as fit on the device
+// at once and each warp walks the tiles with a grid stride; otherwise one warp per tile.
+template <bool kCount, bool kWide, int kMinBlocks>
+__global__ void __launch_bounds__(128, kMinBlocks) render_kernel(const __grid_constant__ RenderParams p) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = (int64_t)p.E * p.tiles_per_env;
+    const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t step = p.step_dev ? *p.step_dev : p.step;
+#pragma unroll 1
+    for (int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); warp < total; warp += stride)
+        render_tile<kCount, kWide>(p, warp, lane, step);
+}
+
+// Graph replays read the step from device memory; this advances it after each replayed render.
+__global__ void advance_step_kernel(int64_t *step) { *step += 1; }
+
 __global__ void set_first_kernel(int64_t *s_first, int32_t E, int64_t step, const uint8_t *mask) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < E && (mask == nullptr || mask[i] != 0)) s_first[i] = step;
@@ -763,19 +795,38 @@ cudaError_t launch_prep(const PrepParams &p, cudaStream_t s) {
 cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
     const int64_t warps = (int64_t)p.E * p.tiles_per_env;
     if (warps == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((warps + 3) / 4);
-    (void)cudaGetLastError();
-    if (p.wide) {
-        if (count)
-            render_kernel<true, true><<<blocks, 128, 0, s>>>(p);
-        else
-            render_kernel<false, true><<<blocks, 128, 0, s>>>(p);
-    } else {
-        if (count)
-            render_kernel<true, false><<<blocks, 128, 0, s>>>(p);
-        else
-            render_kernel<false, false><<<blocks, 128, 0, s>>>(p);
+    const int min_blocks = p.min_blocks == 12 ? 12 : 8;
+    int64_t blocks = (warps + 3) / 4;
+    if (p.persistent) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
+                                                       cudaSuccess && sms > 0)
+            blocks = std::min<int64_t>(blocks, (int64_t)sms * min_blocks);
     }
+    (void)cudaGetLastError();
+    const unsigned g = (unsigned)blocks;
+    if (count) {
+        if (p.wide)
+            render_kernel<true, true, 8><<<g, 128, 0, s>>>(p);
+        else
+            render_kernel<true, false, 8><<<g, 128, 0, s>>>(p);
+    } else if (min_blocks == 12) {
+        if (p.wide)
+            render_kernel<false, true, 12><<<g, 128, 0, s>>>(p);
+        else
+            render_kernel<false, false, 12><<<g, 128, 0, s>>>(p);
+    } else {
+        if (p.wide)
+            render_kernel<false, true, 8><<<g, 128, 0, s>>>(p);
+        else
+            render_kernel<false, false, 8><<<g, 128, 0, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance_step(int64_t *step, cudaStream_t s) {
+    (void)cudaGetLastError();
+    advance_step_kernel<<<1, 1, 0, s>>>(step);
     return cudaGetLastError();
 }
 

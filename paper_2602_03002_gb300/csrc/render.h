@@ -38,8 +38,17 @@ struct PrepParams {
     CamDev cams[RPL_MAX_CAMERAS];
     // latency draw (span = max_latency + 1; 0 or 1 = none)
     int64_t step;
+    const int64_t *step_dev;   // when set, the step is read from device memory (graph replays)
     const int64_t *s_first;
     uint32_t env_offset, span, seed0, seed1;
+};
+
+// Launch shape of the render kernel (chosen by the autotuner or set by the caller).
+struct Tuning {
+    int32_t tile_w_log2;     // tile of 32 rays: width 2^tile_w_log2 (2..4: 4x8, 8x4, 16x2)
+    int32_t persistent;      // grid of resident blocks only, warps stride over the tiles
+    int32_t terrain_first;   // query the terrain before the links
+    int32_t min_blocks;      // 8 (64 registers) or 12 (40 registers) blocks of 128 per SM
 };
 
 struct RenderParams {
@@ -57,8 +66,11 @@ struct RenderParams {
     int32_t pix_per_env, depth_kind;
     int32_t lroot[RPL_MAX_LINKS];   // root node of each link BVH in lnodes, -1 = no mesh
     CamDev cams[RPL_MAX_CAMERAS];
+    // launch shape (see Tuning)
+    int32_t tile_w_log2, persistent, terrain_first, min_blocks;
     // sensor model
     int64_t step;
+    const int64_t *step_dev;        // when set, the step is read from device memory (graph replays)
     uint32_t env_offset, span;      // span = max_latency + 1
     uint32_t seed0, seed1;
     uint64_t drop_thr;              // floor(p_drop 2^32)
@@ -74,6 +86,7 @@ struct RenderParams {
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s);
 cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s);
 cudaError_t launch_set_first(int64_t *s_first, int32_t E, int64_t step, const uint8_t *mask, cudaStream_t s);
+cudaError_t launch_advance_step(int64_t *step, cudaStream_t s);
 
 // Depth of the traversal stack; scenes whose BVH is deeper are refused at build time.
 constexpr int kStackDepth = 64;

@@ -154,6 +154,17 @@ struct rpl_view {
     bool timing = false;
     cudaEvent_t ev[2 * kTimingSlots] = {};
     int64_t n_timed = 0;
+    // launch shape of the render kernel
+    Tuning tune{3, 0, 0, 8};
+    // graph replay (rpl_render_graph): device step counter, captured graph and what it was captured for
+    DevBuf d_step;
+    int64_t dev_step_next = INT64_MIN; // value the device counter holds before the next replay
+    int64_t gen = 0, g_gen = -1;       // bumped by rpl_cameras_set / rpl_sensor_set
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    const void *g_poses = nullptr, *g_out = nullptr;
+    Tuning g_tune{};
+    int64_t g_env_offset = -1;
 };
 
 extern "C" {
@@ -489,6 +500,7 @@ RPL_API rpl_status rpl_cameras_set(rpl_view_t v, const rpl_camera *cams, int32_t
     v->C = n_cams;
     v->P = off;
     v->cams_set = true;
+    v->gen++;
     cudaError_t e = v->cam_xf.alloc((size_t)v->E * n_cams * 5 * sizeof(float4));
     if (e != cudaSuccess) return cuda_fail(e, "rpl_cameras_set: allocating camera transforms");
     if (per_env_intr) {
@@ -527,6 +539,7 @@ RPL_API rpl_status rpl_sensor_set(rpl_view_t v, const rpl_sensor_params *prm) {
         return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_set: unknown out_dtype");
     DeviceGuard g(v->scene->device);
     v->sensor = *prm;
+    v->gen++;
     v->has_last = false;
     v->need_first = true;
     return alloc_ring(v);
@@ -541,14 +554,18 @@ RPL_API rpl_status rpl_view_layout(rpl_view_t v, int64_t *cam_offsets, int64_t *
     return RPL_OK;
 }
 
-static void fill_cams(const rpl_view *v, CamDev *out) {
+// Kernel view of the cameras for the view's tile shape; returns the tiles per env.
+static int32_t fill_cams(const rpl_view *v, CamDev *out) {
+    const int tw = 1 << v->tune.tile_w_log2, th = 32 / tw;
+    int32_t toff = 0;
     for (int c = 0; c < v->C; ++c) {
         const rpl_camera &k = v->cams[c];
         CamDev &d = out[c];
         d.width = k.width;
         d.height = k.height;
-        d.tiles_x = (k.width + 7) / 8;
-        d.tile_off = v->tile_off[c];
+        d.tiles_x = (k.width + tw - 1) / tw;
+        d.tile_off = toff;
+        toff += d.tiles_x * ((k.height + th - 1) / th);
         d.pix_off = (int32_t)v->cam_off[c];
         d.mount = k.mount_link;
         d.fx = k.fx;
@@ -560,15 +577,19 @@ static void fill_cams(const rpl_view *v, CamDev *out) {
         for (int a = 0; a < 3; ++a) d.off_pos[a] = k.offset_pos[a];
         quat_normalise(k.offset_quat_xyzw, d.off_quat);
     }
+    return toff;
 }
 
 static size_t out_elem_bytes(const rpl_view *v) { return v->sensor.out_dtype == RPL_OUT_F32 ? 4 : 2; }
 
+// Enqueues prep + render.  step_dev (graph capture only) makes both kernels read the step from
+// device memory instead of `step`.
 static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int64_t env_offset, void *out_dev,
-                          cudaStream_t st, bool count, unsigned long long *counters_dev) {
+                          cudaStream_t st, bool count, unsigned long long *counters_dev,
+                          const int64_t *step_dev = nullptr) {
     rpl_scene *s = v->scene;
     cudaError_t e;
-    if (v->need_first) {
+    if (v->need_first && !step_dev) {
         e = launch_set_first(v->s_first.as<int64_t>(), v->E, step, nullptr, st);
         if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the sensor-state reset");
         v->need_first = false;
@@ -586,8 +607,9 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
     pp.E = v->E;
     pp.L = v->L;
     pp.C = v->C;
-    fill_cams(v, pp.cams);
+    const int32_t tiles_per_env = fill_cams(v, pp.cams);
     pp.step = step;
+    pp.step_dev = step_dev;
     pp.s_first = v->s_first.as<const int64_t>();
     pp.env_offset = (uint32_t)env_offset;
     pp.span = (uint32_t)v->sensor.max_latency + 1u;
@@ -610,7 +632,12 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
     rp.E = v->E;
     rp.L = v->L;
     rp.C = v->C;
-    rp.tiles_per_env = v->tile_off[v->C];
+    rp.tiles_per_env = tiles_per_env;
+    rp.tile_w_log2 = v->tune.tile_w_log2;
+    rp.persistent = v->tune.persistent;
+    rp.terrain_first = v->tune.terrain_first;
+    rp.min_blocks = v->tune.min_blocks;
+    rp.step_dev = step_dev;
     rp.pix_per_env = (int32_t)v->P;
     rp.depth_kind = v->sensor.depth_kind;
     for (int l = 0; l < RPL_MAX_LINKS; ++l) rp.lroot[l] = l < v->L ? s->l_root[l] : -1;
@@ -633,10 +660,11 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
     rp.err = v->err_dev;
     rp.counters = counters_dev;
     const int slot = (int)(v->n_timed % rpl_view::kTimingSlots);
-    if (v->timing) cudaEventRecord(v->ev[2 * slot], st);
+    const bool timed = v->timing && !step_dev;   // no event records inside a graph capture
+    if (timed) cudaEventRecord(v->ev[2 * slot], st);
     e = launch_render(rp, count, st);
     if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the render kernel");
-    if (v->timing) {
+    if (timed) {
         cudaEventRecord(v->ev[2 * slot + 1], st);
         v->n_timed++;
     }
@@ -820,6 +848,175 @@ RPL_API rpl_status rpl_view_kernel_ms(rpl_view_t v, float *ms, int32_t max_n, in
     return RPL_OK;
 }
 
+static bool tuning_from(const rpl_tuning *t, Tuning *out) {
+    const int lg = t->tile_w == 4 ? 2 : t->tile_w == 8 ? 3 : t->tile_w == 16 ? 4 : -1;
+    if (lg < 0 || t->tile_w * t->tile_h != 32 || (t->min_blocks != 8 && t->min_blocks != 12)) return false;
+    out->tile_w_log2 = lg;
+    out->persistent = t->persistent ? 1 : 0;
+    out->terrain_first = t->terrain_first ? 1 : 0;
+    out->min_blocks = t->min_blocks;
+    return true;
+}
+
+static void tuning_to(const Tuning &t, rpl_tuning *out) {
+    out->tile_w = 1 << t.tile_w_log2;
+    out->tile_h = 32 >> t.tile_w_log2;
+    out->persistent = t.persistent;
+    out->terrain_first = t.terrain_first;
+    out->min_blocks = t.min_blocks;
+}
+
+RPL_API rpl_status rpl_view_tuning_set(rpl_view_t v, const rpl_tuning *t) {
+    if (!v || !t) return fail(RPL_ERR_INVALID_ARG, "rpl_view_tuning_set: NULL argument");
+    Tuning n;
+    if (!tuning_from(t, &n))
+        return fail(RPL_ERR_INVALID_ARG, "rpl_view_tuning_set: tile must be 4x8, 8x4 or 16x2 and min_blocks 8 or 12");
+    v->tune = n;
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_view_tuning_get(rpl_view_t v, rpl_tuning *t) {
+    if (!v || !t) return fail(RPL_ERR_INVALID_ARG, "rpl_view_tuning_get: NULL argument");
+    tuning_to(v->tune, t);
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_view_autotune(rpl_view_t v, const float *poses, int64_t step, int64_t env_offset, void *out,
+                                     void *stream, int32_t reps, rpl_tuning *best, float *best_ms) {
+    rpl_status st = check_render_args(v, poses, env_offset, out);
+    if (st != RPL_OK) return st;
+    if (reps < 1) return fail(RPL_ERR_INVALID_ARG, "rpl_view_autotune: reps must be >= 1");
+    if (v->has_last && step != v->last_step && step != v->last_step + 1)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_view_autotune: step must be the previous step or the next one");
+    if (v->E == 0) {
+        if (best) tuning_to(v->tune, best);
+        if (best_ms) *best_ms = 0.f;
+        return RPL_OK;
+    }
+    rpl_scene *s = v->scene;
+    DeviceGuard g(s->device);
+    if (pointer_kind(poses, s->device) != PTR_DEVICE || pointer_kind(out, s->device) != PTR_DEVICE)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_view_autotune: poses and output must be device memory");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return cuda_fail(e, "rpl_view_autotune: cudaEventCreate");
+    }
+    const Tuning saved = v->tune;
+    const bool saved_timing = v->timing;
+    v->timing = false;
+    Tuning best_t = saved;
+    float best_v = INFINITY;
+    const int tiles[3] = {3, 2, 4};
+    for (int ti = 0; ti < 3 && st == RPL_OK; ++ti)
+        for (int pers = 0; pers < 2 && st == RPL_OK; ++pers)
+            for (int tf = 0; tf < 2 && st == RPL_OK; ++tf)
+                for (int mb = 0; mb < 2 && st == RPL_OK; ++mb) {
+                    v->tune = Tuning{tiles[ti], pers, tf, mb ? 12 : 8};
+                    st = enqueue(v, poses, step, env_offset, out, cs, false, nullptr);   // warm-up
+                    if (st != RPL_OK) break;
+                    cudaEventRecord(a, cs);
+                    for (int r = 0; r < reps && st == RPL_OK; ++r)
+                        st = enqueue(v, poses, step, env_offset, out, cs, false, nullptr);
+                    cudaEventRecord(b, cs);
+                    e = cudaEventSynchronize(b);
+                    float ms = 0.f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+                    if (e != cudaSuccess) st = cuda_fail(e, "rpl_view_autotune: timing");
+                    ms /= (float)reps;
+                    if (st == RPL_OK && ms < best_v) {
+                        best_v = ms;
+                        best_t = v->tune;
+                    }
+                }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    v->timing = saved_timing;
+    v->tune = st == RPL_OK ? best_t : saved;
+    if (st != RPL_OK) return st;
+    v->has_last = true;
+    v->last_step = step;
+    if (best) tuning_to(best_t, best);
+    if (best_ms) *best_ms = best_v;
+    return RPL_OK;
+}
+
+static void graph_release(rpl_view *v) {
+    if (v->gexec) cudaGraphExecDestroy(v->gexec);
+    v->gexec = nullptr;
+}
+
+RPL_API rpl_status rpl_render_graph(rpl_view_t v, const float *poses, int64_t env_offset, void *out, void *stream,
+                                    int64_t *step_out) {
+    rpl_status st = check_render_args(v, poses, env_offset, out);
+    if (st != RPL_OK) return st;
+    const int64_t next = v->has_last ? v->last_step + 1 : 0;
+    if (step_out) *step_out = next;
+    if (v->E == 0) {
+        v->has_last = true;
+        v->last_step = next;
+        return RPL_OK;
+    }
+    rpl_scene *s = v->scene;
+    DeviceGuard g(s->device);
+    if (pointer_kind(poses, s->device) != PTR_DEVICE || pointer_kind(out, s->device) != PTR_DEVICE)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_render_graph: poses and output must be device memory");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (!v->d_step.p) e = v->d_step.alloc(sizeof(int64_t));
+    if (e == cudaSuccess && !v->cap_stream) e = cudaStreamCreateWithFlags(&v->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_render_graph: setting up");
+    if (v->need_first) {
+        e = launch_set_first(v->s_first.as<int64_t>(), v->E, next, nullptr, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "rpl_render_graph: launching the sensor-state reset");
+        v->need_first = false;
+    }
+    const bool same = v->gexec && v->g_poses == poses && v->g_out == out && v->g_env_offset == env_offset &&
+                      v->g_gen == v->gen && std::memcmp(&v->g_tune, &v->tune, sizeof(Tuning)) == 0;
+    if (!same) {
+        graph_release(v);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(v->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "rpl_render_graph: cudaStreamBeginCapture");
+        st = enqueue(v, poses, next, env_offset, out, v->cap_stream, false, nullptr, v->d_step.as<const int64_t>());
+        if (st == RPL_OK) {
+            e = launch_advance_step(v->d_step.as<int64_t>(), v->cap_stream);
+            if (e != cudaSuccess) st = cuda_fail(e, "rpl_render_graph: capturing the step advance");
+        }
+        const cudaError_t ec = cudaStreamEndCapture(v->cap_stream, &graph);
+        if (st == RPL_OK && ec != cudaSuccess) st = cuda_fail(ec, "rpl_render_graph: cudaStreamEndCapture");
+        if (st == RPL_OK) {
+            e = cudaGraphInstantiate(&v->gexec, graph, 0);
+            if (e != cudaSuccess) {
+                v->gexec = nullptr;
+                st = cuda_fail(e, "rpl_render_graph: cudaGraphInstantiate");
+            }
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (st != RPL_OK) return st;
+        v->g_poses = poses;
+        v->g_out = out;
+        v->g_env_offset = env_offset;
+        v->g_gen = v->gen;
+        v->g_tune = v->tune;
+    }
+    if (v->dev_step_next != next) {
+        // the counter is out of step (first replay, or rpl_render ran in between): set it in stream order
+        e = launch_set_first(v->d_step.as<int64_t>(), 1, next, nullptr, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "rpl_render_graph: setting the step counter");
+    }
+    e = cudaGraphLaunch(v->gexec, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_render_graph: cudaGraphLaunch");
+    v->dev_step_next = next + 1;
+    v->has_last = true;
+    v->last_step = next;
+    v->last_stream = cs;
+    return RPL_OK;
+}
+
 RPL_API void rpl_view_destroy(rpl_view_t v) {
     if (!v) return;
     {
@@ -828,6 +1025,8 @@ RPL_API void rpl_view_destroy(rpl_view_t v) {
         if (v->err_host) cudaFreeHost(v->err_host);
         for (int i = 0; i < 2 * rpl_view::kTimingSlots; ++i)
             if (v->ev[i]) cudaEventDestroy(v->ev[i]);
+        graph_release(v);
+        if (v->cap_stream) cudaStreamDestroy(v->cap_stream);
         std::lock_guard<std::mutex> lk(v->scene->mu);
         v->scene->views--;
         delete v;

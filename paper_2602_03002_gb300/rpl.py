@@ -57,6 +57,14 @@ class rpl_scene_info(ctypes.Structure):
                 ("link_depth", ctypes.c_int32), ("frozen", ctypes.c_int32)]
 
 
+class rpl_tuning(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("terrain_first", ctypes.c_int32), ("min_blocks", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 class rpl_counters(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("rays", "terrain_nodes", "terrain_tris", "link_boxes",
                                                 "link_nodes", "link_tris")]
@@ -65,7 +73,8 @@ class rpl_counters(ctypes.Structure):
 EXPORTS = ["rpl_bvh_build_host", "rpl_bvh8_build_host", "rpl_scene_create", "rpl_link_mesh_add", "rpl_scene_info_get", "rpl_scene_destroy", "rpl_view_create",
            "rpl_cameras_set", "rpl_sensor_set", "rpl_view_layout", "rpl_render", "rpl_view_reset", "rpl_sync",
            "rpl_render_counters", "rpl_view_timing", "rpl_view_kernel_ms", "rpl_view_destroy", "rpl_last_error",
-           "rpl_version", "rpl_render_static_scratch"]
+           "rpl_version", "rpl_render_static_scratch", "rpl_view_tuning_set", "rpl_view_tuning_get",
+           "rpl_view_autotune", "rpl_render_graph"]
 
 _lib = None
 
@@ -100,6 +109,10 @@ def lib() -> ctypes.CDLL:
         "rpl_last_error": ([], ctypes.c_char_p),
         "rpl_version": ([], I32),
         "rpl_render_static_scratch": ([P, P, I32, I32, I32, P, P, I64, I64, P, P], I32),
+        "rpl_view_tuning_set": ([P, P], I32),
+        "rpl_view_tuning_get": ([P, P], I32),
+        "rpl_view_autotune": ([P, P, I64, I64, P, P, I32, P, P], I32),
+        "rpl_render_graph": ([P, P, I64, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -274,6 +287,35 @@ def rpl_render_static_scratch(scene: int, cams: Sequence, n_envs: int, n_links: 
     sen = None if sensor is None else ctypes.byref(_sensor_struct(sensor))
     _check(lib().rpl_render_static_scratch(scene, arr, len(cams), int(n_envs), int(n_links), _ptr(poses), sen,
                                            int(step), int(env_offset), _ptr(out), _stream_handle(stream)))
+
+
+def rpl_view_tuning_set(view: int, tile_w: int = 8, tile_h: int = 4, persistent: int = 0, terrain_first: int = 0,
+                        min_blocks: int = 8):
+    t = rpl_tuning(tile_w, tile_h, persistent, terrain_first, min_blocks)
+    _check(lib().rpl_view_tuning_set(view, ctypes.byref(t)))
+
+
+def rpl_view_tuning_get(view: int) -> dict:
+    t = rpl_tuning()
+    _check(lib().rpl_view_tuning_get(view, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def rpl_view_autotune(view: int, poses, step: int, env_offset: int, out, stream=None, reps: int = 3):
+    """Times the 24 launch shapes, keeps the fastest on the view; returns (tuning dict, ms per render)."""
+    t = rpl_tuning()
+    ms = ctypes.c_float()
+    _check(lib().rpl_view_autotune(view, _ptr(poses), int(step), int(env_offset), _ptr(out), _stream_handle(stream),
+                                   int(reps), ctypes.byref(t), ctypes.byref(ms)))
+    return t.as_dict(), float(ms.value)
+
+
+def rpl_render_graph(view: int, poses, env_offset: int, out, stream=None) -> int:
+    """Replays the captured graph of the whole path for the next step; returns that step."""
+    s = ctypes.c_int64()
+    _check(lib().rpl_render_graph(view, _ptr(poses), int(env_offset), _ptr(out), _stream_handle(stream),
+                                  ctypes.byref(s)))
+    return int(s.value)
 
 
 def rpl_view_destroy(view: int):

@@ -472,10 +472,11 @@ def config_scale(n_steps: int = 4, n_envs: int = 4096, tiles: int = 20, cell: fl
                     sensor if sensor is not None else scale_sensor())
 
 
-def config_uneven(n_steps: int = 4, n_envs: int = 4096, tiles: int = 20, cell: float = 0.05) -> Workload:
+def config_uneven(n_steps: int = 4, n_envs: int = 4096, tiles: int = 20, cell: float = 0.05,
+                  seed: int = 0) -> Workload:
     """4096 envs x 4 uneven cameras (front/back 80x60, left/right 48x36), FP32 depth, no sensor."""
     return config_scale(n_steps, n_envs, tiles, cell, ((80, 60), (80, 60), (48, 36), (48, 36)),
-                        sensor=Sensor())
+                        sensor=Sensor(), seed=seed)
 
 
 def make_workload(name: str, **kw) -> Workload:

@@ -1,0 +1,120 @@
+"""Batching: uneven cameras in one launch, launch shapes chosen by the autotuner, graph replay.
+
+The launch shape (tile of 32 rays, persistent grid-stride loop, query order, registers per thread)
+must never change the depth: every one of the 24 shapes gives bit-identical frames, also on ragged
+cameras where tiles hang over the image edge.  Replaying the captured graph of the whole path must
+continue the sensor history exactly like step-by-step rpl_render calls.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import compare_depth
+from paper_2602_03002_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [dict(tile_w=tw, tile_h=32 // tw, persistent=p, terrain_first=tf, min_blocks=mb)
+          for tw, p, tf, mb in itertools.product((8, 4, 16), (0, 1), (0, 1), (8, 12))]
+
+
+def _ragged(w):
+    torso = w.cameras[0].mount_link
+    w.cameras = [W.pinhole(13, 7, 80.0, 50.0, torso, (0.10, 0.0, 0.30), 0.0, 45.0, 0.1, 3.0),
+                 W.pinhole(21, 11, 90.0, 60.0, torso, (-0.10, 0.0, 0.30), 180.0, 40.0, 0.2, 2.5),
+                 W.pinhole(3, 2, 60.0, 40.0, 0, (0.0, 0.15, 0.1), 90.0, 30.0, 0.05, 4.0)]
+    return w
+
+
+@pytest.mark.parametrize("ragged", [False, True])
+def test_every_launch_shape_gives_identical_depth(cuda, rpl_lib, ragged):
+    torch = cuda
+    w = W.config_small(n_steps=2)
+    if ragged:
+        w = _ragged(w)
+    sen = W.Sensor(sigma_abs=0.01, p_drop=0.05, max_latency=2, seed=(1, 2))
+    scene = rpl_lib.Scene.from_workload(w)
+    view = rpl_lib.View(scene, w.n_envs, w.n_links)
+    view.set_cameras(w.cameras)
+    view.set_sensor(sen)
+    poses = torch.from_numpy(w.poses).cuda()
+    view.render(poses[0], 0)
+    ref = view.render(poses[1], 1).clone()
+    for shape in SHAPES:
+        rpl_lib.rpl_view_tuning_set(view.h, **shape)
+        assert rpl_lib.rpl_view_tuning_get(view.h) == shape
+        out = view.render(poses[1], 1)                      # re-render the same step
+        assert torch.equal(out, ref), shape
+    view.sync()
+
+
+def test_graph_replay_continues_the_sensor_history(cuda, rpl_lib):
+    torch = cuda
+    w = W.config_small(n_steps=8)
+    sen = W.Sensor(sigma_abs=0.01, p_drop=0.05, max_latency=3, seed=(31, 32))
+    scene = rpl_lib.Scene.from_workload(w)
+    poses = torch.from_numpy(w.poses).cuda()
+    a = rpl_lib.View.from_workload(scene, w)
+    a.set_sensor(sen)
+    ref = [a.render(poses[s], s).clone() for s in range(8)]
+    b = rpl_lib.View.from_workload(scene, w)
+    b.set_sensor(sen)
+    rpl_lib.rpl_view_tuning_set(b.h, tile_w=16, tile_h=2, persistent=1)
+    stream = torch.cuda.Stream()
+    pose_buf = torch.empty_like(poses[0])
+    out = b.out_tensor()
+    got = []
+    with torch.cuda.stream(stream):
+        for s in range(6):
+            pose_buf.copy_(poses[s])
+            step = rpl_lib.rpl_render_graph(b.h, pose_buf, 0, out, stream)
+            assert step == s
+            got.append(out.clone())
+        # a plain render in between, then replays again
+        got.append(b.render(poses[6], 6, 0, None, stream).clone())
+        pose_buf.copy_(poses[7])
+        assert rpl_lib.rpl_render_graph(b.h, pose_buf, 0, out, stream) == 7
+        got.append(out.clone())
+    stream.synchronize()
+    b.sync()
+    for s in range(8):
+        assert torch.equal(got[s], ref[s]), s
+
+
+def test_autotune_picks_a_shape_and_keeps_results(cuda, rpl_lib):
+    torch = cuda
+    w = W.config_small(n_steps=1)
+    scene = rpl_lib.Scene.from_workload(w)
+    view = rpl_lib.View.from_workload(scene, w)
+    poses = torch.from_numpy(w.poses[0]).cuda()
+    ref = view.render(poses, 0).clone()
+    out = torch.empty_like(ref)
+    best, ms = rpl_lib.rpl_view_autotune(view.h, poses, 0, 0, out, None, 2)
+    assert best in SHAPES and ms > 0
+    assert rpl_lib.rpl_view_tuning_get(view.h) == best
+    assert torch.equal(view.render(poses, 0), ref)
+
+
+def test_uneven_four_cameras_vs_oracle(cuda, rpl_lib):
+    """The batching configuration's camera set (front/back 80x60, left/right 48x36) on a small scene."""
+    torch = cuda
+    w = W.config_uneven(n_steps=1, n_envs=6, tiles=1, cell=0.2)
+    scene = rpl_lib.Scene.from_workload(w)
+    view = rpl_lib.View.from_workload(scene, w)
+    offs, total = view.layout()
+    assert offs == [0, 4800, 9600, 11328, 13056] and total == 13056
+    poses = torch.from_numpy(w.poses[0]).cuda()
+    best, _ = rpl_lib.rpl_view_autotune(view.h, poses, 0, 0, view.out_tensor(), None, 1)
+    out = view.render(poses, 0).cpu().numpy()
+    rng = np.random.default_rng(12)
+    rays = oracle.all_rays(w.cameras, w.n_envs)
+    rays = rays[rng.choice(len(rays), 4000, replace=False)]
+    osc = oracle.OracleScene.from_workload(w)
+    ref = osc.render(w.cameras, w.poses, 0, rays, w.sensor)
+    o = np.asarray(offs)
+    cam_w = np.array([c.width for c in w.cameras])
+    got = out[rays[:, 0], o[rays[:, 1]] + rays[:, 3] * cam_w[rays[:, 1]] + rays[:, 2]]
+    compare_depth(got, ref["depth"], ref["flags"], "uneven cameras")
+    assert np.mean(ref["depth"] < 3.0) > 0.3
