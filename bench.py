@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--tiles", type=int, default=20)
     ap.add_argument("--pose-sets", type=int, default=8)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed launch shape tile_w,tile_h,persistent,terrain_first,min_blocks (skips the autotuner)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the oracle sample")
@@ -98,12 +100,15 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(rays, variant):
-    """DRAM bytes per launch from the committed ncu capture, scaled by rays; None if the kernel changed."""
+def traffic_per_launch(rays, variant, tuning):
+    """DRAM bytes per launch from the committed ncu capture, scaled by rays; None if the kernel, the
+    variant or the launch shape differ from what was captured."""
     try:
         with open(TRAFFIC) as f:
             t = json.load(f)
         if t.get("kernel_sha") != kernel_hash() or t.get("variant", "plain") != variant:
+            return None
+        if t.get("tuning") is not None and t["tuning"] != tuning:
             return None
         return float(t["dram_bytes"]) * rays / float(t["rays"])
     except Exception:
@@ -265,7 +270,11 @@ def run_ours(args):
     alg_bytes = b_nodes + b_tris + b_boxes + b_io
 
     tuning, tune_ms = rpl.rpl_view_tuning_get(view.h), None
-    if not args.no_autotune:
+    if args.tuning:
+        tw, th, pers, tf, mb = (int(v) for v in args.tuning.split(","))
+        rpl.rpl_view_tuning_set(view.h, tw, th, pers, tf, mb)
+        tuning = rpl.rpl_view_tuning_get(view.h)
+    elif not args.no_autotune:
         with torch.cuda.stream(stream):
             tuning, tune_ms = rpl.rpl_view_autotune(view.h, poses[0], 0, env_offset, out, stream, 3)
     view.reset(None, 0)
@@ -358,7 +367,7 @@ def run_ours(args):
         "env_steps_per_s": world * w.n_envs / (ms_step / 1e3),
         "gpu_launches": (3 if graph else 2) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_per_launch(rays, args.variant),
+                     "frac": achieved / peak, "traffic": traffic_per_launch(rays, args.variant, tuning),
                      "kernel": "render_kernel", "kernel_ms": 1e3 * k_avg_s,
                      "kernel_ms_source": "CUDA events around each render launch" if kms else
                                          "whole graph replay (events cannot be recorded inside the graph)",
