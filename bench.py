@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variant", default="plain", choices=["plain", "precision", "batching"])
+    ap.add_argument("--variant", default="plain", choices=["plain", "precision", "batching", "serving"])
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--tiles", type=int, default=20)
     ap.add_argument("--pose-sets", type=int, default=8)
@@ -389,10 +389,137 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_serving(args):
+    """Config 5: Poisson streams of render requests from 4 trainer threads (4 views each: env counts
+    log-uniform in 64..8192, 1-4 cameras front/back 64x48, left/right 48x36), one resident scene.
+    The same seeded arrival schedule is served by the continuous-batching server and by plain
+    per-request launches (a server with batches of one on one stream); latency is submit to
+    completion on the host clock."""
+    import threading
+    import torch
+    from paper_2602_03002_gb300 import build as B, rpl, workloads as W
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    B.build()
+    base = W.config_scale(n_steps=1, n_envs=16, tiles=args.tiles)
+    scene = rpl.Scene(base.terrain_verts, base.terrain_tris, device=local)
+    for l, (v_, t_) in enumerate(zip(base.link_verts, base.link_tris)):
+        scene.add_link(l, v_, t_)
+    rng = np.random.default_rng(5)
+    n_tr, per_tr = 4, 4
+    sizes = [(64, 48), (64, 48), (48, 36), (48, 36)]
+    shapes = []
+    for k in range(n_tr * per_tr):
+        E = int(round(float(np.exp(rng.uniform(np.log(64), np.log(8192))))))
+        C = int(rng.integers(1, 5))
+        poses, cams = W.scale_envs(E, 4, args.tiles, sizes[:C], seed=100 + k)
+        shapes.append((E, cams, torch.from_numpy(poses).cuda()))
+    sensor = W.scale_sensor()
+
+    def make_views():
+        vs = []
+        for k, (E, cams, poses) in enumerate(shapes):
+            v = rpl.View(scene, E, 30)
+            v.set_cameras(cams)
+            v.set_sensor(sensor)
+            vs.append((v, v.out_tensor(), poses, E * sum(c.width * c.height for c in cams)))
+        return vs
+
+    # calibration: mean time of one request rendered alone
+    vs = make_views()
+    times = []
+    for k, (v, out, poses, rays) in enumerate(vs):
+        for s in range(3):
+            v.render(poses[s % 4], s, 0, out)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for s in range(3, 6):
+            v.render(poses[s % 4], s, 0, out)
+        torch.cuda.synchronize()
+        times.append((time.perf_counter() - t) / 3)
+    del vs
+    service = float(np.mean(times))
+    load = 0.8
+    rate = load / service                       # requests per second, all trainers together
+    n_req = max(40, args.steps * 4)
+    sched = []
+    for tr in range(n_tr):
+        gaps = rng.exponential(n_tr / rate, size=n_req // n_tr)
+        sched.append(np.cumsum(gaps))
+
+    def run_mode(max_batch, n_streams):
+        vs = make_views()
+        server = rpl.Server(scene, max_batch=max_batch, n_streams=n_streams)
+        lat, rays_done = [], [0]
+        lock = threading.Lock()
+        steps = [0] * len(vs)
+        t0 = time.perf_counter() + 0.05
+
+        def trainer(tr):
+            import queue as q
+            pending = q.Queue()
+
+            def waiter():
+                while True:
+                    item = pending.get()
+                    if item is None:
+                        return
+                    tk, rays = item
+                    dt = server.wait(tk)
+                    with lock:
+                        lat.append(dt)
+                        rays_done[0] += rays
+            w_th = threading.Thread(target=waiter)
+            w_th.start()
+            for i, ta in enumerate(sched[tr]):
+                k = tr * per_tr + i % per_tr
+                v, out, poses, rays = vs[k]
+                now = time.perf_counter()
+                if t0 + ta > now:
+                    time.sleep(t0 + ta - now)
+                s = steps[k]
+                steps[k] += 1
+                pending.put((server.submit(v, poses[s % 4], s, out), rays))
+            pending.put(None)
+            w_th.join()
+
+        th = [threading.Thread(target=trainer, args=(tr,)) for tr in range(n_tr)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        wall = time.perf_counter() - t0
+        st = server.stats()
+        server.close()
+        lat_ms = np.asarray(lat) * 1e3
+        return {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "mean_ms": float(lat_ms.mean()), "requests": len(lat), "grays_per_s": rays_done[0] / wall / 1e9,
+                "wall_s": wall, "batches": st["batches"], "mean_batch": st["fused_requests"] / max(1, st["batches"]),
+                "max_batch_seen": st["max_batch_seen"], "max_inflight_batches": st["max_inflight_batches_seen"]}
+
+    batched = run_mode(32, 2)
+    plain = run_mode(1, 1)
+    line = {"metric": METRIC, "value": batched["grays_per_s"], "unit": "Grays/s", "n_gpus": 1,
+            "steps": n_req, "warmup": 3, "ms_per_step": batched["mean_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "variant": "serving",
+            "config": {"workload": "serving: 4 trainers x 4 views (env counts log-uniform 64..8192, 1-4 cameras "
+                                   "64x48/48x36), Poisson arrivals at %.0f%% of the per-request capacity, %d-tri "
+                                   "terrain resident, sensor on" % (100 * load, len(base.terrain_tris)),
+                       "views": [{"envs": E, "cams": len(c)} for E, c, _ in shapes],
+                       "arrival_rate_per_s": rate, "service_ms_alone": 1e3 * service},
+            "serve": batched, "serve_baseline_per_request": plain,
+            "p50_ms": batched["p50_ms"], "p99_ms": batched["p99_ms"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.variant == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -165,7 +165,9 @@ RPL_API rpl_status rpl_bvh8_build_host(const float *verts, int64_t n_verts, cons
                                        int64_t n_tris, int32_t max_leaf, int32_t threads, void *nodes_out,
                                        int64_t nodes_cap, void *tris_out, int64_t *n_nodes, int32_t *depth);
 
-/* Frees the scene's device memory.  Views of the scene must be destroyed first. */
+/* Frees the scene's device memory.  While views or servers of the scene still exist the scene
+ * stays alive and is freed when the last of them is destroyed (so destruction order, e.g. in a
+ * garbage-collected binding, never matters); it must not be used for new views meanwhile. */
 RPL_API void rpl_scene_destroy(rpl_scene_t scene);
 
 /* ---------------------------------------------------------------------------------------------
@@ -252,6 +254,66 @@ RPL_API rpl_status rpl_view_autotune(rpl_view_t view, const float *link_poses, i
 RPL_API rpl_status rpl_render_graph(rpl_view_t view, const float *link_poses, int64_t env_offset,
                                     void *depth_out, void *stream, int64_t *step_out);
 
+/* ---------------------------------------------------------------------------------------------
+ * Render server: continuous batching of requests from many trainers (not part of the paper's
+ * method; it serves the renderer to several training processes or threads at once).
+ * ------------------------------------------------------------------------------------------- */
+typedef struct rpl_server *rpl_server_t;
+
+/* max_batch: requests fused into one render launch (1..64, 0 = 32); n_streams: batches that may be
+ * on the GPU at once (1..8, 0 = 2); staging_bytes: device memory budget for the pose and depth
+ * staging of requests made with host buffers (0 = 256 MiB) -- a request is admitted only when its
+ * staging fits; min_blocks, persistent: launch shape of the fused launch (see rpl_tuning; 0 = 8,
+ * not persistent). */
+typedef struct {
+    int32_t max_batch;
+    int32_t n_streams;
+    int64_t staging_bytes;
+    int32_t min_blocks;
+    int32_t persistent;
+} rpl_server_opts;
+
+typedef struct {
+    uint64_t submitted, completed, failed, cancelled, batches, fused_requests;
+    int64_t staging_peak_bytes;
+    int32_t max_batch_seen, max_inflight_batches_seen;
+} rpl_server_stats;
+
+/* A server for views of `scene`, with a worker thread that, while requests are waiting, admits them
+ * in arrival order as stream slots and staging memory free up (at most one request per view on the
+ * GPU at a time, since a view's ring buffer and scratch are stateful), fuses the admitted ones into
+ * one launch (one prep launch per request, one render launch over the tiles of all of them) on a
+ * free stream, and completes them when that launch's event has passed; batches on different
+ * streams overlap on the device.  A request's result is the same as rpl_render of the same view
+ * and step alone.  The scene must be frozen (a view created).  Errors: INVALID_ARG, CUDA,
+ * OUT_OF_MEMORY. */
+RPL_API rpl_status rpl_server_create(rpl_scene_t scene, const rpl_server_opts *opts, rpl_server_t *out);
+
+/* Queue a render of `view` at `step` (the view's previous submitted step or that + 1, or any step
+ * for its first request) into depth_out; link_poses and depth_out are host (staged through the
+ * server's budget) or device memory; they and the view must stay valid (not destroyed) until the
+ * request completes: rpl_server_wait returned for it, or, for a cancelled request, the server was
+ * destroyed.  While a view has requests in a server it must not be rendered by other calls.  *ticket identifies the
+ * request.  Errors: INVALID_ARG, CAPACITY (the request's staging exceeds the whole budget). */
+RPL_API rpl_status rpl_server_submit(rpl_server_t server, rpl_view_t view, const float *link_poses, int64_t step,
+                                     int64_t env_offset, void *depth_out, uint64_t *ticket);
+
+/* Wait up to timeout_ms (< 0: forever) for a request; on completion returns its status, sets
+ * *latency_s (submit to completion, host clock; may be NULL) and forgets the ticket.  Returns
+ * RPL_ERR_TIMEOUT when it is still pending (the ticket stays valid), INVALID_ARG for an unknown
+ * ticket. */
+RPL_API rpl_status rpl_server_wait(rpl_server_t server, uint64_t ticket, int32_t timeout_ms, double *latency_s);
+
+/* Give up on a request: it still renders (so the view's step sequence stays whole) and is forgotten
+ * when it completes; waiting on the ticket afterwards returns INVALID_ARG.  For callers that stop
+ * waiting, e.g. a trainer that is shutting down. */
+RPL_API rpl_status rpl_server_cancel(rpl_server_t server, uint64_t ticket);
+
+RPL_API rpl_status rpl_server_stats_get(rpl_server_t server, rpl_server_stats *stats);
+
+/* Stops admitting, waits for the batches on the GPU, fails requests still queued, frees. */
+RPL_API void rpl_server_destroy(rpl_server_t server);
+
 /* Restart the sensor history at `step` for the envs whose byte in env_mask (host or device,
  * [n_envs] uint8) is non-zero, or for all envs when env_mask is NULL: from then on the source step
  * of those envs is never older than `step`.  With a mask, `step` must be the next step to render
@@ -259,8 +321,9 @@ RPL_API rpl_status rpl_render_graph(rpl_view_t view, const float *link_poses, in
  * `stream`.  Errors: INVALID_ARG, CUDA. */
 RPL_API rpl_status rpl_view_reset(rpl_view_t view, const uint8_t *env_mask, int64_t step, void *stream);
 
-/* Wait for the view's work on its last stream, then report and clear a recorded kernel error
- * (DEVICE_FAULT), or a CUDA error. */
+/* Wait until the view's most recently enqueued work (render, reset, graph replay or a server's
+ * batch) has finished, on whichever stream it went (the stream may since have been destroyed),
+ * then report and clear a recorded kernel error (DEVICE_FAULT), or a CUDA error. */
 RPL_API rpl_status rpl_sync(rpl_view_t view);
 
 /* Render like rpl_render (device buffers only) with the counting kernel variant, synchronise, and

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "librpl.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["render.cu", "rpl_api.cpp", "bvh_build.cpp", "bvh8.cpp", "noalloc.cu"]
+SOURCES = ["render.cu", "rpl_api.cpp", "bvh_build.cpp", "bvh8.cpp", "noalloc.cu", "server.cpp"]
 HEADERS = ["bvh.h", "bvh8.h", "render.h", "scene_access.h"]
 
 

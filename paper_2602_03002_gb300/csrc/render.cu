@@ -774,6 +774,29 @@ __global__ void __launch_bounds__(128, kMinBlocks) render_kernel(const __grid_co
         render_tile<kCount, kWide>(p, warp, lane, step);
 }
 
+// Several render requests (each with its own view, envs, cameras and sensor) in one launch: the
+// tiles of request r occupy warps [prefix[r], prefix[r + 1]); each warp finds its request by binary
+// search and renders one tile with that request's parameters (read from global memory).
+template <bool kWide, int kMinBlocks>
+__global__ void __launch_bounds__(128, kMinBlocks)
+    render_multi_kernel(const RenderParams *__restrict__ reqs, const int64_t *__restrict__ prefix, int n_req) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = prefix[n_req];
+    const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 5);
+#pragma unroll 1
+    for (int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); warp < total; warp += stride) {
+        int lo = 0, hi = n_req - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= warp) lo = mid;
+            else hi = mid - 1;
+        }
+        const RenderParams &p = reqs[lo];
+        const int64_t step = p.step_dev ? *p.step_dev : p.step;
+        render_tile<false, kWide>(p, warp - prefix[lo], lane, step);
+    }
+}
+
 // Graph replays read the step from device memory; this advances it after each replayed render.
 __global__ void advance_step_kernel(int64_t *step) { *step += 1; }
 
@@ -820,6 +843,33 @@ cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
             render_kernel<false, true, 8><<<g, 128, 0, s>>>(p);
         else
             render_kernel<false, false, 8><<<g, 128, 0, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_multi(const RenderParams *reqs_dev, const int64_t *prefix_dev, int n_req,
+                                int64_t total_warps, bool wide, int min_blocks, bool persistent, cudaStream_t s) {
+    if (total_warps <= 0 || n_req <= 0) return cudaSuccess;
+    int64_t blocks = (total_warps + 3) / 4;
+    const int mb = min_blocks == 12 ? 12 : 8;
+    if (persistent) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
+                                                       cudaSuccess && sms > 0)
+            blocks = std::min<int64_t>(blocks, (int64_t)sms * mb);
+    }
+    (void)cudaGetLastError();
+    const unsigned g = (unsigned)blocks;
+    if (wide) {
+        if (mb == 12)
+            render_multi_kernel<true, 12><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
+        else
+            render_multi_kernel<true, 8><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
+    } else {
+        if (mb == 12)
+            render_multi_kernel<false, 12><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
+        else
+            render_multi_kernel<false, 8><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
     }
     return cudaGetLastError();
 }

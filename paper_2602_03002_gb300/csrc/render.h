@@ -87,6 +87,10 @@ cudaError_t launch_prep(const PrepParams &p, cudaStream_t s);
 cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s);
 cudaError_t launch_set_first(int64_t *s_first, int32_t E, int64_t step, const uint8_t *mask, cudaStream_t s);
 cudaError_t launch_advance_step(int64_t *step, cudaStream_t s);
+// One launch over several requests: reqs_dev[n_req] parameters in device memory, prefix_dev[n_req + 1]
+// the first warp of each request (prefix_dev[n_req] = total_warps).
+cudaError_t launch_render_multi(const RenderParams *reqs_dev, const int64_t *prefix_dev, int n_req,
+                                int64_t total_warps, bool wide, int min_blocks, bool persistent, cudaStream_t s);
 
 // Depth of the traversal stack; scenes whose BVH is deeper are refused at build time.
 constexpr int kStackDepth = 64;

@@ -129,7 +129,9 @@ struct rpl_scene {
     int64_t l_n_nodes = 0, l_n_tris = 0;
     int32_t l_depth = 0;
     bool frozen = false;
-    int views = 0;
+    int views = 0;                  // views and servers still using the scene
+    int servers = 0;
+    bool destroy_pending = false;   // rpl_scene_destroy came while they existed
     std::mutex mu;
 };
 
@@ -148,7 +150,10 @@ struct rpl_view {
     bool has_last = false;
     int64_t last_step = 0;
     bool need_first = true;        // s_first must be set by the next render
-    cudaStream_t last_stream = nullptr;
+    // recorded on the stream of every enqueued render or reset: rpl_sync and rpl_view_destroy wait on
+    // it, which stays valid after the caller (or a server) has destroyed that stream
+    cudaEvent_t done = nullptr;
+    bool has_done = false;
     // optional timing of the traversal kernel: event pairs recorded around each launch
     static constexpr int kTimingSlots = 256;
     bool timing = false;
@@ -418,8 +423,33 @@ RPL_API rpl_status rpl_bvh8_build_host(const float *verts, int64_t n_verts, cons
 
 RPL_API void rpl_scene_destroy(rpl_scene_t s) {
     if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->views > 0 || s->servers > 0) {
+            s->destroy_pending = true;   // freed by the last view or server that goes
+            return;
+        }
+    }
     DeviceGuard g(s->device);
     delete s;
+}
+
+// Drops one user of the scene (a view or a server) and frees the scene if it was destroyed while
+// in use and this was its last user.
+static void scene_release(rpl_scene *s, bool server) {
+    bool free_now;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (server)
+            s->servers--;
+        else
+            s->views--;
+        free_now = s->destroy_pending && s->views == 0 && s->servers == 0;
+    }
+    if (free_now) {
+        DeviceGuard g(s->device);
+        delete s;
+    }
 }
 
 RPL_API rpl_status rpl_view_create(rpl_scene_t s, int32_t n_envs, int32_t n_links, rpl_view_t *out) {
@@ -448,8 +478,10 @@ RPL_API rpl_status rpl_view_create(rpl_scene_t s, int32_t n_envs, int32_t n_link
         *v->err_host = 0;
         e = cudaHostGetDevicePointer((void **)&v->err_dev, v->err_host, 0);
     }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         if (v->err_host) cudaFreeHost(v->err_host);
+        if (v->done) cudaEventDestroy(v->done);
         delete v;
         return cuda_fail(e, "rpl_view_create: allocating per-env state");
     }
@@ -582,11 +614,17 @@ static int32_t fill_cams(const rpl_view *v, CamDev *out) {
 
 static size_t out_elem_bytes(const rpl_view *v) { return v->sensor.out_dtype == RPL_OUT_F32 ? 4 : 2; }
 
-// Enqueues prep + render.  step_dev (graph capture only) makes both kernels read the step from
-// device memory instead of `step`.
-static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int64_t env_offset, void *out_dev,
-                          cudaStream_t st, bool count, unsigned long long *counters_dev,
-                          const int64_t *step_dev = nullptr) {
+// Prep and render parameters of one render of view v (device buffers); launches the sensor-state
+// reset on `st` first when the view needs one.  step_dev (graph capture only) makes both kernels
+// read the step from device memory instead of `step`.
+// Marks the end of the work just enqueued for `v` on `st`.
+static void mark_done(rpl_view *v, cudaStream_t st) {
+    if (cudaEventRecord(v->done, st) == cudaSuccess) v->has_done = true;
+}
+
+static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step, int64_t env_offset, void *out_dev,
+                               cudaStream_t st, unsigned long long *counters_dev, const int64_t *step_dev,
+                               PrepParams &pp, RenderParams &rp) {
     rpl_scene *s = v->scene;
     cudaError_t e;
     if (v->need_first && !step_dev) {
@@ -594,7 +632,7 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
         if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the sensor-state reset");
         v->need_first = false;
     }
-    PrepParams pp{};
+    pp = PrepParams{};
     pp.poses = poses_dev;
     pp.link_root = s->l_roots.as<const float4>();
     pp.tnodes = s->t_nodes.as<const float4>();
@@ -615,10 +653,8 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
     pp.span = (uint32_t)v->sensor.max_latency + 1u;
     pp.seed0 = v->sensor.seed[0];
     pp.seed1 = v->sensor.seed[1];
-    e = launch_prep(pp, st);
-    if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the prep kernel");
 
-    RenderParams rp{};
+    rp = RenderParams{};
     rp.tnodes = s->t_nodes.as<const float4>();
     rp.ttris = s->t_tris.as<const float4>();
     rp.wide = pp.wide;
@@ -659,6 +695,19 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
     rp.out = out_dev;
     rp.err = v->err_dev;
     rp.counters = counters_dev;
+    return RPL_OK;
+}
+
+// Enqueues prep + render of view v on `st`.
+static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int64_t env_offset, void *out_dev,
+                          cudaStream_t st, bool count, unsigned long long *counters_dev,
+                          const int64_t *step_dev = nullptr) {
+    PrepParams pp;
+    RenderParams rp;
+    rpl_status stt = build_params(v, poses_dev, step, env_offset, out_dev, st, counters_dev, step_dev, pp, rp);
+    if (stt != RPL_OK) return stt;
+    cudaError_t e = launch_prep(pp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the prep kernel");
     const int slot = (int)(v->n_timed % rpl_view::kTimingSlots);
     const bool timed = v->timing && !step_dev;   // no event records inside a graph capture
     if (timed) cudaEventRecord(v->ev[2 * slot], st);
@@ -668,7 +717,7 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
         cudaEventRecord(v->ev[2 * slot + 1], st);
         v->n_timed++;
     }
-    v->last_stream = st;
+    if (!step_dev) mark_done(v, st);   // a captured render is marked by rpl_render_graph's launch
     return RPL_OK;
 }
 
@@ -802,14 +851,14 @@ RPL_API rpl_status rpl_view_reset(rpl_view_t v, const uint8_t *mask, int64_t ste
     }
     e = launch_set_first(v->s_first.as<int64_t>(), v->E, step, md, cs);
     if (e != cudaSuccess) return cuda_fail(e, "rpl_view_reset: launch");
-    v->last_stream = cs;
+    mark_done(v, cs);
     return RPL_OK;
 }
 
 RPL_API rpl_status rpl_sync(rpl_view_t v) {
     if (!v) return fail(RPL_ERR_INVALID_ARG, "rpl_sync: view is NULL");
     DeviceGuard g(v->scene->device);
-    cudaError_t e = cudaStreamSynchronize(v->last_stream);
+    cudaError_t e = v->has_done ? cudaEventSynchronize(v->done) : cudaSuccess;
     if (e != cudaSuccess) return cuda_fail(e, "rpl_sync");
     int32_t w = *(volatile int32_t *)v->err_host;
     if (w != 0) {
@@ -1013,7 +1062,7 @@ RPL_API rpl_status rpl_render_graph(rpl_view_t v, const float *poses, int64_t en
     v->dev_step_next = next + 1;
     v->has_last = true;
     v->last_step = next;
-    v->last_stream = cs;
+    mark_done(v, cs);
     return RPL_OK;
 }
 
@@ -1021,16 +1070,17 @@ RPL_API void rpl_view_destroy(rpl_view_t v) {
     if (!v) return;
     {
         DeviceGuard g(v->scene->device);
-        if (v->last_stream) cudaStreamSynchronize(v->last_stream);
+        if (v->has_done) cudaEventSynchronize(v->done);
+        if (v->done) cudaEventDestroy(v->done);
         if (v->err_host) cudaFreeHost(v->err_host);
         for (int i = 0; i < 2 * rpl_view::kTimingSlots; ++i)
             if (v->ev[i]) cudaEventDestroy(v->ev[i]);
         graph_release(v);
         if (v->cap_stream) cudaStreamDestroy(v->cap_stream);
-        std::lock_guard<std::mutex> lk(v->scene->mu);
-        v->scene->views--;
-        delete v;
     }
+    rpl_scene *s = v->scene;
+    delete v;
+    scene_release(s, false);
 }
 
 }  // extern "C"
@@ -1053,5 +1103,46 @@ bool scene_inputs(const rpl_scene *s, SceneInputs *out) {
 }
 
 rpl_status set_error(rpl_status st, const char *msg) { return fail(st, "%s", msg); }
+
+rpl_status view_validate(rpl_view *v, const float *poses, int64_t env_offset, void *out) {
+    return check_render_args(v, poses, env_offset, out);
+}
+
+bool view_step_allowed(const rpl_view *v, int64_t step) {
+    return !v->has_last || step == v->last_step || step == v->last_step + 1;
+}
+
+rpl_status view_prepare(rpl_view *v, const float *poses_dev, int64_t step, int64_t env_offset, void *out_dev,
+                        cudaStream_t st, RenderParams *rp, int64_t *warps) {
+    PrepParams pp;
+    rpl_status s = build_params(v, poses_dev, step, env_offset, out_dev, st, nullptr, nullptr, pp, *rp);
+    if (s != RPL_OK) return s;
+    cudaError_t e = launch_prep(pp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the prep kernel");
+    *warps = (int64_t)rp->E * rp->tiles_per_env;
+    return RPL_OK;
+}
+
+void view_commit(rpl_view *v, int64_t step, cudaStream_t st) {
+    v->has_last = true;
+    v->last_step = step;
+    mark_done(v, st);
+}
+
+size_t view_pose_bytes(const rpl_view *v) { return (size_t)v->E * v->L * 7 * sizeof(float); }
+size_t view_out_bytes(const rpl_view *v) { return (size_t)v->E * v->P * out_elem_bytes(v); }
+int32_t view_envs(const rpl_view *v) { return v->E; }
+rpl_scene *view_scene(const rpl_view *v) { return v->scene; }
+Tuning view_tuning(const rpl_view *v) { return v->tune; }
+int scene_device_of(const rpl_scene *s) { return s->device; }
+bool scene_is_wide(const rpl_scene *s) { return s->opts.bvh_kind == RPL_BVH8Q8; }
+bool pointer_on_device(const void *p, int device) { return pointer_kind(p, device) == PTR_DEVICE; }
+
+void scene_add_server(rpl_scene *s) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->servers++;
+}
+
+void scene_remove_server(rpl_scene *s) { scene_release(s, true); }
 
 }  // namespace rpl

@@ -1,9 +1,10 @@
-// scene_access.h -- read-only view of a frozen scene's device data for entry points that live in
-// other translation units than rpl_api.cpp.
+// scene_access.h -- what entry points outside rpl_api.cpp (the no-allocation render, the render
+// server) may use of scenes and views, without depending on their layout.
 #pragma once
 #include <cuda_runtime.h>
 
 #include "../../include/rpl.h"
+#include "render.h"
 
 namespace rpl {
 
@@ -20,5 +21,24 @@ bool scene_inputs(const rpl_scene *s, SceneInputs *out);
 
 // Records the message returned by rpl_last_error() and returns `st`.
 rpl_status set_error(rpl_status st, const char *msg);
+
+// Views, for the render server (server.cpp).  view_prepare launches the sensor-state reset (when
+// due) and the prep kernel on `st` and fills the render parameters; warps = tiles of the request.
+rpl_status view_validate(rpl_view *v, const float *poses, int64_t env_offset, void *out);
+bool view_step_allowed(const rpl_view *v, int64_t step);
+rpl_status view_prepare(rpl_view *v, const float *poses_dev, int64_t step, int64_t env_offset, void *out_dev,
+                        cudaStream_t st, RenderParams *rp, int64_t *warps);
+void view_commit(rpl_view *v, int64_t step, cudaStream_t st);
+size_t view_pose_bytes(const rpl_view *v);
+size_t view_out_bytes(const rpl_view *v);
+int32_t view_envs(const rpl_view *v);
+rpl_scene *view_scene(const rpl_view *v);
+Tuning view_tuning(const rpl_view *v);
+int scene_device_of(const rpl_scene *s);
+bool scene_is_wide(const rpl_scene *s);
+bool pointer_on_device(const void *p, int device);
+// A server keeps its scene alive: rpl_scene_destroy is deferred until the last server (and view) goes.
+void scene_add_server(rpl_scene *s);
+void scene_remove_server(rpl_scene *s);
 
 }  // namespace rpl

@@ -1,0 +1,495 @@
+// server.cpp -- continuous-batching render server (rpl_server_* in include/rpl.h).
+//
+// Trainers submit render requests (a view, a step, pose and depth buffers) from any thread.  A
+// worker thread admits waiting requests in arrival order whenever a stream slot is free, skipping
+// (without reordering) requests whose view already has work on the GPU or whose host-buffer
+// staging does not fit the device budget, fuses the admitted ones into one launch -- one prep
+// launch per request, then one render launch over the tiles of all of them -- and completes them
+// when the launch's event has passed.  Batches on different slots overlap on the device, so
+// requests that arrive while others run are admitted as soon as a slot and memory free up.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "../../include/rpl.h"
+#include "render.h"
+#include "scene_access.h"
+
+using namespace rpl;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+constexpr size_t kAlign = 256;
+
+size_t round_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
+
+// First-fit allocator over the byte range [0, size) of the staging arena.
+class Arena {
+public:
+    void reset(size_t size) {
+        free_.clear();
+        if (size) free_[0] = size;
+        used_ = 0;
+    }
+    bool alloc(size_t n, size_t *off) {
+        n = round_up(n);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            *off = it->first;
+            const size_t rest = it->second - n, start = it->first + n;
+            free_.erase(it);
+            if (rest) free_[start] = rest;
+            used_ += n;
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        n = round_up(n);
+        used_ -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t used() const { return used_; }
+
+private:
+    std::map<size_t, size_t> free_;   // offset -> length of free ranges
+    size_t used_ = 0;
+};
+
+constexpr size_t kNone = ~(size_t)0;
+
+struct Request {
+    uint64_t id = 0;
+    rpl_view *view = nullptr;
+    const float *poses = nullptr;
+    void *out = nullptr;
+    int64_t step = 0, env_offset = 0;
+    bool poses_host = false, out_host = false;
+    size_t pose_bytes = 0, out_bytes = 0, pose_off = kNone, out_off = kNone;
+    Clock::time_point t_submit, t_done;
+    rpl_status status = RPL_OK;
+    std::string err;
+    bool done = false, cancelled = false;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    RenderParams *h_params = nullptr;   // pinned
+    int64_t *h_prefix = nullptr;        // pinned
+    RenderParams *d_params = nullptr;
+    int64_t *d_prefix = nullptr;
+    bool busy = false;
+    std::vector<Request *> reqs;
+};
+
+}  // namespace
+
+struct rpl_server {
+    rpl_scene *scene = nullptr;
+    int device = 0;
+    bool wide = false;
+    rpl_server_opts opts{};
+    unsigned char *arena_dev = nullptr;
+    Arena arena;
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> queue;
+    std::unordered_map<uint64_t, Request *> tickets;
+    std::unordered_map<rpl_view *, int64_t> last_submitted;
+    std::unordered_set<rpl_view *> on_gpu;   // views with a request in a busy slot
+    uint64_t next_id = 1;
+    bool stop = false;
+    int inflight = 0;
+    rpl_server_stats stats{};
+    bool registered = false;   // counted as a user of the scene
+    std::thread worker;
+};
+
+namespace {
+
+// Fills slot s with the admitted batch and launches it (called without the server lock).
+void launch_batch(rpl_server *sv, Slot &s) {
+    cudaStream_t st = s.stream;
+    const int n = (int)s.reqs.size();
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        Request *r = s.reqs[i];
+        s.h_prefix[i] = total;
+        const float *pd = r->poses_host ? reinterpret_cast<const float *>(sv->arena_dev + r->pose_off) : r->poses;
+        void *od = r->out_host ? (void *)(sv->arena_dev + r->out_off) : r->out;
+        if (r->poses_host) {
+            cudaError_t e = cudaMemcpyAsync(const_cast<float *>(pd), r->poses, r->pose_bytes, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) {
+                r->status = RPL_ERR_CUDA;
+                r->err = cudaGetErrorString(e);
+                continue;
+            }
+        }
+        int64_t warps = 0;
+        rpl_status stt = view_prepare(r->view, pd, r->step, r->env_offset, od, st, &s.h_params[i], &warps);
+        if (stt != RPL_OK) {
+            r->status = stt;
+            r->err = rpl_last_error();
+            continue;
+        }
+        view_commit(r->view, r->step, st);
+        total += warps;
+    }
+    s.h_prefix[n] = total;
+    cudaError_t e = cudaMemcpyAsync(s.d_params, s.h_params, (size_t)n * sizeof(RenderParams), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.d_prefix, s.h_prefix, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_render_multi(s.d_params, s.d_prefix, n, total, sv->wide, sv->opts.min_blocks,
+                                sv->opts.persistent != 0, st);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        Request *r = s.reqs[i];
+        if (r->out_host && r->status == RPL_OK)
+            e = cudaMemcpyAsync(r->out, sv->arena_dev + r->out_off, r->out_bytes, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(s.done, st);
+    if (e != cudaSuccess) {
+        for (Request *r : s.reqs)
+            if (r->status == RPL_OK) {
+                r->status = RPL_ERR_CUDA;
+                r->err = cudaGetErrorString(e);
+            }
+        cudaStreamSynchronize(st);   // let anything that did launch finish before the slot is reused
+        cudaGetLastError();
+        cudaEventRecord(s.done, st);
+    }
+}
+
+void release_staging(rpl_server *sv, Request *r) {
+    if (r->pose_off != kNone) sv->arena.release(r->pose_off, r->pose_bytes);
+    if (r->out_off != kNone) sv->arena.release(r->out_off, r->out_bytes);
+    r->pose_off = r->out_off = kNone;
+}
+
+// Marks r done (lock held); a cancelled request is forgotten right away.
+void finish(rpl_server *sv, Request *r, Clock::time_point now) {
+    r->done = true;
+    r->t_done = now;
+    if (r->status == RPL_OK)
+        sv->stats.completed++;
+    else
+        sv->stats.failed++;
+    if (r->cancelled) {
+        sv->tickets.erase(r->id);
+        delete r;
+    }
+}
+
+// Completes the batches whose event has passed (lock held).
+void poll_slots(rpl_server *sv) {
+    bool any = false;
+    for (Slot &s : sv->slots) {
+        if (!s.busy) continue;
+        const cudaError_t q = cudaEventQuery(s.done);
+        if (q == cudaErrorNotReady) continue;
+        const Clock::time_point now = Clock::now();
+        for (Request *r : s.reqs) {
+            if (q != cudaSuccess && r->status == RPL_OK) {
+                r->status = RPL_ERR_CUDA;
+                r->err = cudaGetErrorString(q);
+            }
+            release_staging(sv, r);
+            sv->on_gpu.erase(r->view);
+            finish(sv, r, now);
+        }
+        if (q != cudaSuccess) cudaGetLastError();
+        s.reqs.clear();
+        s.busy = false;
+        sv->inflight--;
+        any = true;
+    }
+    if (any) sv->cv_done.notify_all();
+}
+
+void worker_main(rpl_server *sv) {
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    for (;;) {
+        poll_slots(sv);
+        if (sv->stop) {
+            // fail what never reached the GPU, then drain the slots
+            const Clock::time_point now = Clock::now();
+            while (!sv->queue.empty()) {
+                Request *r = sv->queue.front();
+                sv->queue.pop_front();
+                r->status = RPL_ERR_INVALID_ARG;
+                r->err = "rpl_server: the server was destroyed before the request was admitted";
+                finish(sv, r, now);
+            }
+            sv->cv_done.notify_all();
+            if (sv->inflight == 0) break;
+            sv->cv_work.wait_for(lk, std::chrono::microseconds(100));
+            continue;
+        }
+        int free_slot = -1;
+        for (size_t i = 0; i < sv->slots.size(); ++i)
+            if (!sv->slots[i].busy) {
+                free_slot = (int)i;
+                break;
+            }
+        if (free_slot >= 0 && !sv->queue.empty()) {
+            Slot &s = sv->slots[free_slot];
+            std::unordered_set<rpl_view *> blocked;   // views whose earlier request waits: keep their order
+            for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)s.reqs.size() < sv->opts.max_batch;) {
+                Request *r = *it;
+                if (blocked.count(r->view) || sv->on_gpu.count(r->view)) {
+                    blocked.insert(r->view);
+                    ++it;
+                    continue;
+                }
+                bool ok = true;
+                if (r->poses_host && !sv->arena.alloc(r->pose_bytes, &r->pose_off)) ok = false;
+                if (ok && r->out_host && !sv->arena.alloc(r->out_bytes, &r->out_off)) ok = false;
+                if (!ok) {
+                    release_staging(sv, r);
+                    blocked.insert(r->view);
+                    ++it;
+                    continue;
+                }
+                sv->on_gpu.insert(r->view);
+                s.reqs.push_back(r);
+                it = sv->queue.erase(it);
+            }
+            if (!s.reqs.empty()) {
+                s.busy = true;
+                sv->inflight++;
+                sv->stats.batches++;
+                sv->stats.fused_requests += s.reqs.size();
+                sv->stats.max_batch_seen = std::max(sv->stats.max_batch_seen, (int32_t)s.reqs.size());
+                sv->stats.max_inflight_batches_seen = std::max(sv->stats.max_inflight_batches_seen, (int32_t)sv->inflight);
+                sv->stats.staging_peak_bytes = std::max(sv->stats.staging_peak_bytes, (int64_t)sv->arena.used());
+                lk.unlock();
+                launch_batch(sv, s);
+                lk.lock();
+                continue;
+            }
+        }
+        if (sv->inflight > 0)
+            sv->cv_work.wait_for(lk, std::chrono::microseconds(100));   // poll the busy slots' events
+        else
+            sv->cv_work.wait(lk, [&] { return sv->stop || !sv->queue.empty(); });
+    }
+}
+
+rpl_status server_fail(rpl_status st, const std::string &msg) { return set_error(st, msg.c_str()); }
+
+}  // namespace
+
+extern "C" {
+
+RPL_API rpl_status rpl_server_create(rpl_scene_t scene, const rpl_server_opts *opts, rpl_server_t *out) {
+    if (!out) return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_create: out is NULL");
+    *out = nullptr;
+    SceneInputs si;
+    if (!scene_inputs(scene, &si))
+        return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_create: scene is NULL or not frozen (create a view first)");
+    rpl_server_opts o{};
+    if (opts) o = *opts;
+    if (o.max_batch == 0) o.max_batch = 32;
+    if (o.n_streams == 0) o.n_streams = 2;
+    if (o.staging_bytes == 0) o.staging_bytes = (int64_t)256 << 20;
+    if (o.min_blocks == 0) o.min_blocks = 8;
+    if (o.max_batch < 1 || o.max_batch > 64 || o.n_streams < 1 || o.n_streams > 8 || o.staging_bytes < 0 ||
+        (o.min_blocks != 8 && o.min_blocks != 12))
+        return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_create: max_batch 1..64, n_streams 1..8, "
+                                                "staging_bytes >= 0, min_blocks 8 or 12");
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(si.device);
+    rpl_server *sv = new (std::nothrow) rpl_server();
+    if (!sv) return server_fail(RPL_ERR_OUT_OF_MEMORY, "rpl_server_create: host allocation");
+    sv->scene = scene;
+    sv->device = si.device;
+    sv->wide = si.wide != 0;
+    sv->opts = o;
+    cudaError_t e = cudaMalloc(&sv->arena_dev, std::max<size_t>((size_t)o.staging_bytes, kAlign));
+    sv->arena.reset((size_t)o.staging_bytes);
+    sv->slots.resize(o.n_streams);
+    for (Slot &s : sv->slots) {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaHostAlloc(&s.h_params, o.max_batch * sizeof(RenderParams), cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaHostAlloc(&s.h_prefix, (o.max_batch + 1) * sizeof(int64_t), cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaMalloc(&s.d_params, o.max_batch * sizeof(RenderParams));
+        if (e == cudaSuccess) e = cudaMalloc(&s.d_prefix, (o.max_batch + 1) * sizeof(int64_t));
+    }
+    if (e != cudaSuccess) {
+        rpl_server_destroy(sv);
+        if (prev >= 0) cudaSetDevice(prev);
+        return server_fail(e == cudaErrorMemoryAllocation ? RPL_ERR_OUT_OF_MEMORY : RPL_ERR_CUDA,
+                           std::string("rpl_server_create: ") + cudaGetErrorString(e));
+    }
+    scene_add_server(scene);
+    sv->registered = true;
+    sv->worker = std::thread(worker_main, sv);
+    if (prev >= 0) cudaSetDevice(prev);
+    *out = sv;
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_server_submit(rpl_server_t sv, rpl_view_t view, const float *poses, int64_t step,
+                                     int64_t env_offset, void *out, uint64_t *ticket) {
+    if (!sv || !view || !ticket) return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_submit: NULL argument");
+    if (view_scene(view) != sv->scene)
+        return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_submit: the view belongs to another scene");
+    rpl_status st = view_validate(view, poses, env_offset, out);
+    if (st != RPL_OK) return st;
+    Request *r = new (std::nothrow) Request();
+    if (!r) return server_fail(RPL_ERR_OUT_OF_MEMORY, "rpl_server_submit: host allocation");
+    r->view = view;
+    r->poses = poses;
+    r->out = out;
+    r->step = step;
+    r->env_offset = env_offset;
+    r->pose_bytes = view_pose_bytes(view);
+    r->out_bytes = view_out_bytes(view);
+    {
+        int prev = -1;
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        cudaSetDevice(sv->device);
+        r->poses_host = view_envs(view) > 0 && !pointer_on_device(poses, sv->device);
+        r->out_host = view_envs(view) > 0 && !pointer_on_device(out, sv->device);
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    const size_t staging = (r->poses_host ? round_up(r->pose_bytes) : 0) + (r->out_host ? round_up(r->out_bytes) : 0);
+    if (staging > (size_t)sv->opts.staging_bytes) {
+        delete r;
+        return server_fail(RPL_ERR_CAPACITY, "rpl_server_submit: the request's host-buffer staging exceeds the "
+                                             "server's whole staging budget");
+    }
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->stop) {
+            delete r;
+            return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_submit: the server is stopping");
+        }
+        auto it = sv->last_submitted.find(view);
+        const bool order_ok = it != sv->last_submitted.end() ? (step == it->second || step == it->second + 1)
+                                                             : view_step_allowed(view, step);
+        if (!order_ok) {
+            delete r;
+            return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_submit: a view's steps must advance by 0 or 1");
+        }
+        r->id = sv->next_id++;
+        sv->last_submitted[view] = step;
+        sv->stats.submitted++;
+        sv->tickets[r->id] = r;
+        if (view_envs(view) == 0) {
+            finish(sv, r, Clock::now());   // nothing to render
+        } else {
+            sv->queue.push_back(r);
+        }
+        *ticket = r->id;
+    }
+    sv->cv_work.notify_one();
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_server_wait(rpl_server_t sv, uint64_t ticket, int32_t timeout_ms, double *latency_s) {
+    if (!sv) return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_wait: server is NULL");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    if (it == sv->tickets.end() || it->second->cancelled)
+        return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_wait: unknown ticket");
+    Request *r = it->second;
+    auto pred = [&] { return r->done; };
+    if (timeout_ms < 0)
+        sv->cv_done.wait(lk, pred);
+    else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
+        return server_fail(RPL_ERR_TIMEOUT, "rpl_server_wait: the request is still pending");
+    const rpl_status st = r->status;
+    const std::string err = r->err;
+    if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+    sv->tickets.erase(it);
+    delete r;
+    if (st != RPL_OK) return server_fail(st, err);
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_server_cancel(rpl_server_t sv, uint64_t ticket) {
+    if (!sv) return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_cancel: server is NULL");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    if (it == sv->tickets.end()) return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_cancel: unknown ticket");
+    Request *r = it->second;
+    sv->stats.cancelled++;
+    if (r->done) {
+        sv->tickets.erase(it);
+        delete r;
+    } else {
+        r->cancelled = true;   // it still renders (the view's step sequence stays whole), then is forgotten
+    }
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_server_stats_get(rpl_server_t sv, rpl_server_stats *stats) {
+    if (!sv || !stats) return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_stats_get: NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    *stats = sv->stats;
+    return RPL_OK;
+}
+
+RPL_API void rpl_server_destroy(rpl_server_t sv) {
+    if (!sv) return;
+    if (sv->worker.joinable()) {
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->stop = true;
+        }
+        sv->cv_work.notify_all();
+        sv->worker.join();
+    }
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(sv->device);
+    for (Slot &s : sv->slots) {
+        if (s.stream) cudaStreamSynchronize(s.stream);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.stream) cudaStreamDestroy(s.stream);
+        if (s.h_params) cudaFreeHost(s.h_params);
+        if (s.h_prefix) cudaFreeHost(s.h_prefix);
+        if (s.d_params) cudaFree(s.d_params);
+        if (s.d_prefix) cudaFree(s.d_prefix);
+    }
+    if (sv->arena_dev) cudaFree(sv->arena_dev);
+    for (auto &kv : sv->tickets) delete kv.second;
+    if (prev >= 0) cudaSetDevice(prev);
+    rpl_scene *scene = sv->registered ? sv->scene : nullptr;
+    delete sv;
+    if (scene) scene_remove_server(scene);
+}
+
+}  // extern "C"

@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librpl.so")
 
 RPL_OK = 0
+RPL_ERR_TIMEOUT = 6
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "NOT_FOUND", 5: "CAPACITY",
            6: "TIMEOUT", 7: "DEVICE_FAULT"}
 RPL_MAX_CAMERAS = 8
@@ -65,6 +66,18 @@ class rpl_tuning(ctypes.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
+class rpl_server_opts(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("n_streams", ctypes.c_int32), ("staging_bytes", ctypes.c_int64),
+                ("min_blocks", ctypes.c_int32), ("persistent", ctypes.c_int32)]
+
+
+class rpl_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "cancelled", "batches",
+                                                "fused_requests")] + \
+               [("staging_peak_bytes", ctypes.c_int64), ("max_batch_seen", ctypes.c_int32),
+                ("max_inflight_batches_seen", ctypes.c_int32)]
+
+
 class rpl_counters(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("rays", "terrain_nodes", "terrain_tris", "link_boxes",
                                                 "link_nodes", "link_tris")]
@@ -74,7 +87,8 @@ EXPORTS = ["rpl_bvh_build_host", "rpl_bvh8_build_host", "rpl_scene_create", "rpl
            "rpl_cameras_set", "rpl_sensor_set", "rpl_view_layout", "rpl_render", "rpl_view_reset", "rpl_sync",
            "rpl_render_counters", "rpl_view_timing", "rpl_view_kernel_ms", "rpl_view_destroy", "rpl_last_error",
            "rpl_version", "rpl_render_static_scratch", "rpl_view_tuning_set", "rpl_view_tuning_get",
-           "rpl_view_autotune", "rpl_render_graph"]
+           "rpl_view_autotune", "rpl_render_graph", "rpl_server_create", "rpl_server_submit", "rpl_server_wait",
+           "rpl_server_cancel", "rpl_server_stats_get", "rpl_server_destroy"]
 
 _lib = None
 
@@ -113,6 +127,12 @@ def lib() -> ctypes.CDLL:
         "rpl_view_tuning_get": ([P, P], I32),
         "rpl_view_autotune": ([P, P, I64, I64, P, P, I32, P, P], I32),
         "rpl_render_graph": ([P, P, I64, P, P, P], I32),
+        "rpl_server_create": ([P, P, P], I32),
+        "rpl_server_submit": ([P, P, P, I64, I64, P, P], I32),
+        "rpl_server_wait": ([P, ctypes.c_uint64, I32, P], I32),
+        "rpl_server_cancel": ([P, ctypes.c_uint64], I32),
+        "rpl_server_stats_get": ([P, P], I32),
+        "rpl_server_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -419,6 +439,91 @@ class View:
         if getattr(self, "h", None):
             rpl_view_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------------------------------
+# Render server (continuous batching across trainers)
+# --------------------------------------------------------------------------------------------------
+def rpl_server_create(scene: int, max_batch: int = 0, n_streams: int = 0, staging_bytes: int = 0, min_blocks: int = 0,
+                      persistent: int = 0) -> int:
+    o = rpl_server_opts(max_batch, n_streams, staging_bytes, min_blocks, persistent)
+    h = ctypes.c_void_p()
+    _check(lib().rpl_server_create(scene, ctypes.byref(o), ctypes.byref(h)))
+    return h.value
+
+
+def rpl_server_submit(server: int, view: int, poses, step: int, env_offset: int, out) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().rpl_server_submit(server, view, _ptr(poses), int(step), int(env_offset), _ptr(out), ctypes.byref(t)))
+    return int(t.value)
+
+
+def rpl_server_wait(server: int, ticket: int, timeout_ms: int = -1) -> float:
+    """Waits for a request; returns its latency in seconds (raises RplError, TIMEOUT when still pending)."""
+    lat = ctypes.c_double()
+    _check(lib().rpl_server_wait(server, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(lat)))
+    return float(lat.value)
+
+
+def rpl_server_cancel(server: int, ticket: int):
+    _check(lib().rpl_server_cancel(server, ctypes.c_uint64(ticket)))
+
+
+def rpl_server_stats_get(server: int) -> dict:
+    s = rpl_server_stats()
+    _check(lib().rpl_server_stats_get(server, ctypes.byref(s)))
+    return {f: int(getattr(s, f)) for f, _ in rpl_server_stats._fields_}
+
+
+def rpl_server_destroy(server: int):
+    lib().rpl_server_destroy(server)
+
+
+class Server:
+    """Owner of a render server for views of `scene` (see rpl_server_create)."""
+
+    def __init__(self, scene: Scene, **opts):
+        self.scene = scene
+        self._held = {}      # ticket -> (view, poses, out): kept alive until the request completes
+        self._cancelled = []
+        self.h = rpl_server_create(scene.h, **opts)
+
+    def submit(self, view: View, poses, step: int, out, env_offset: int = 0) -> int:
+        ticket = rpl_server_submit(self.h, view.h, poses, step, env_offset, out)
+        self._held[ticket] = (view, poses, out)
+        return ticket
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> float:
+        try:
+            dt = rpl_server_wait(self.h, ticket, timeout_ms)
+        except RplError as e:
+            if e.status != RPL_ERR_TIMEOUT:
+                self._held.pop(ticket, None)
+            raise
+        self._held.pop(ticket, None)
+        return dt
+
+    def cancel(self, ticket: int):
+        rpl_server_cancel(self.h, ticket)
+        held = self._held.pop(ticket, None)
+        if held is not None:
+            self._cancelled.append(held)   # it may still render: released when the server is closed
+
+    def stats(self) -> dict:
+        return rpl_server_stats_get(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            rpl_server_destroy(self.h)
+            self.h = None
+        self._held = {}
+        self._cancelled = []
 
     def __del__(self):
         try:

@@ -456,6 +456,17 @@ def config_scale(n_steps: int = 4, n_envs: int = 4096, tiles: int = 20, cell: fl
     tv, tt = _scale_terrain(tiles, cell)
     links, torso = _robot(30)
     lv, lt = _link_meshes(links, "ellipsoid")
+    poses, cams = scale_envs(n_envs, n_steps, tiles, cam_sizes, seed)
+    return Workload("scale: %d envs x %d cams, %d-tri terrain (%dx%d tiles at %.2f m), 30 x 512-tri links"
+                    % (n_envs, len(cams), len(tt), tiles, tiles, cell), tv, tt, lv, lt, cams, poses,
+                    sensor if sensor is not None else scale_sensor())
+
+
+def scale_envs(n_envs: int, n_steps: int, tiles: int = 20,
+               cam_sizes: Sequence[Tuple[int, int]] = ((64, 48), (64, 48)), seed: int = 0):
+    """Poses [S, E, 30, 7] of envs spread over the tiled terrain (env e on tile e mod tiles^2, uniform in
+    its inner 5x5 m, 0.75 m above the ground, uniform yaw) and the torso cameras; no mesh is built."""
+    links, torso = _robot(30)
     rng = np.random.default_rng(seed + 2)
     tile = np.arange(n_envs) % (tiles * tiles)
     ti, tj = tile // tiles, tile % tiles
@@ -466,10 +477,7 @@ def config_scale(n_steps: int = 4, n_envs: int = 4096, tiles: int = 20, cell: fl
     h = scale_terrain_height(x, y, tiles)
     root = np.stack([x, y, h + 0.75], axis=1)
     poses = _pose_sequence(links, root, yaw, n_steps, np.random.default_rng(seed + 1))
-    cams = _torso_cameras(torso, list(cam_sizes))
-    return Workload("scale: %d envs x %d cams, %d-tri terrain (%dx%d tiles at %.2f m), 30 x 512-tri links"
-                    % (n_envs, len(cams), len(tt), tiles, tiles, cell), tv, tt, lv, lt, cams, poses,
-                    sensor if sensor is not None else scale_sensor())
+    return poses, _torso_cameras(torso, list(cam_sizes))
 
 
 def config_uneven(n_steps: int = 4, n_envs: int = 4096, tiles: int = 20, cell: float = 0.05,
