@@ -1,5 +1,5 @@
 #!/usr/bin/env python3
-"""Benchmark of multi-depth ray casting + sensor model (Sec. 3.2.1, Algorithm 1, Appendix A.2).
+"""Benchmark of multi-depth ray casting + sensor model (Sec. 3.2.2, Algorithm 1, Appendix A.2).
 
 Variants (``--variant``):
   plain      4096 envs x 2 cameras x 64x48 px, 20.48M-triangle terrain, 30 links of 512 triangles,

@@ -5,7 +5,7 @@
  * cameras mounted on a robot by casting one ray per pixel against one shared static terrain
  * triangle mesh and against that environment's own posed robot-link meshes, then applies a depth
  * sensor model (latency ring buffer, additive noise, pixel dropout, range clipping).
- * It follows Sec. 3.2.1 ("Efficient Multi-Depth System Simulation") and Algorithm 1 of
+ * It follows Sec. 3.2.2 ("Efficient Multi-Depth System Simulation") and Algorithm 1 of
  * "RPL: Learning Robust Humanoid Perceptive Locomotion on Challenging Terrains" (arXiv 2602.03002),
  * and the perception rows of its domain-randomisation table (Appendix A.2).
  *
@@ -80,7 +80,7 @@ typedef struct {
 } rpl_scene_opts;
 
 /* Pinhole camera.  Pixel (x, y), 0 <= x < width, 0 <= y < height, has the camera-frame ray
- * r = ((x - cx)/fx, (y - cy)/fy, 1) (Sec. 3.2.1: r_c = K^-1 [x, y, 1]^T).  The camera pose is the
+ * r = ((x - cx)/fx, (y - cy)/fy, 1) (Sec. 3.2.2: r_c = K^-1 [x, y, 1]^T).  The camera pose is the
  * pose of link `mount_link` composed with (offset_pos, offset_quat_xyzw).  Depths are clipped to
  * [d_min, d_max]; a ray that hits nothing closer than d_max reports d_max (the far plane). */
 typedef struct {
@@ -131,7 +131,7 @@ typedef struct {
  * Scene
  * ------------------------------------------------------------------------------------------- */
 
-/* Build the BVH of the static terrain (world frame) once and upload it (Sec. 3.2.1: the terrain is
+/* Build the BVH of the static terrain (world frame) once and upload it (Sec. 3.2.2: the terrain is
  * one shared static mesh).  verts: [n_verts, 3] float32, tris: [n_tris, 3] int32 vertex indices,
  * both host or device.  n_tris may be 0 (nothing but links is hit).  opts may be NULL.
  * Errors: INVALID_ARG (index out of range, negative size), NOT_FOUND, OUT_OF_MEMORY, CUDA. */
@@ -139,7 +139,7 @@ RPL_API rpl_status rpl_scene_create(const float *verts, int64_t n_verts, const i
                                     int64_t n_tris, const rpl_scene_opts *opts, rpl_scene_t *out);
 
 /* Add the mesh of link `link_id` (0 <= link_id < RPL_MAX_LINKS) in its own frame and build its BVH
- * once (Sec. 3.2.1: body meshes stay canonical in their local frames, rays are moved instead, so
+ * once (Sec. 3.2.2: body meshes stay canonical in their local frames, rays are moved instead, so
  * nothing is refitted per frame).  Links without a mesh are never hit.  verts/tris as in
  * rpl_scene_create, host or device.  Must come before the first rpl_view_create on the scene,
  * which freezes it (INVALID_ARG afterwards). */
@@ -181,7 +181,7 @@ RPL_API rpl_status rpl_view_create(rpl_scene_t scene, int32_t n_envs, int32_t n_
 
 /* Set the cameras (1..RPL_MAX_CAMERAS; they may differ in size).  per_env_intrinsics, host or
  * device, is NULL or [n_envs, n_cams, 4] float32 (fx, fy, cx, cy) overriding each camera's
- * intrinsics per env (Sec. 3.2.1: batched inverse intrinsics for per-env FOV randomisation).
+ * intrinsics per env (Sec. 3.2.2: batched inverse intrinsics for per-env FOV randomisation).
  * Restarts the sensor state (as rpl_view_reset with no mask).  Errors: INVALID_ARG (size <= 0,
  * fx or fy == 0, mount_link out of range, d_min > d_max), CAPACITY, OUT_OF_MEMORY. */
 RPL_API rpl_status rpl_cameras_set(rpl_view_t view, const rpl_camera *cams, int32_t n_cams,
@@ -241,7 +241,7 @@ RPL_API rpl_status rpl_view_autotune(rpl_view_t view, const float *link_poses, i
                                      int64_t env_offset, void *depth_out, void *stream, int32_t reps,
                                      rpl_tuning *best, float *best_ms);
 
-/* Render the next step by replaying a CUDA graph of the whole path (Sec. 3.2.1: the pipeline is
+/* Render the next step by replaying a CUDA graph of the whole path (Sec. 3.2.2: the pipeline is
  * captured into a CUDA graph for low-overhead replay).  The first call, and any call after the
  * buffers, env_offset, cameras, sensor or tuning changed, captures prep + render + a step-advance
  * kernel into a graph (on a view-owned stream) and instantiates it; every call then launches it on

@@ -3,7 +3,7 @@
 Only the tests, the package smoke check and the benchmark's CPU-baseline leg import this package.
 It wraps ``oracle.c`` (plain C, OpenMP over rays) through ctypes.  It shares no code with the CUDA
 path: the only common module is the seeded workload generator, which holds none of the method's
-arithmetic.  See ``oracle.c`` for what is computed and the passages it follows (Sec. 3.2.1,
+arithmetic.  See ``oracle.c`` for what is computed and the passages it follows (Sec. 3.2.2,
 Algorithm 1, Appendix A.2).
 """
 from __future__ import annotations
@@ -24,6 +24,7 @@ FLAG_EDGE_1E6 = 2
 FLAG_FAR = 4
 FLAG_DROPPED = 8
 FLAG_GRAZING = 16
+FLAG_MASKED = 32
 # rays on which FP32 arithmetic may legitimately decide differently from the FP64 oracle
 FLAG_FP32_SENSITIVE = 1 | 4 | 16
 
@@ -55,7 +56,7 @@ def lib():
         L.oracle_scene_destroy.restype = None
         L.oracle_render.argtypes = [P, P, P, ctypes.c_int32, P, P, ctypes.c_int64, ctypes.c_int32,
                                     ctypes.c_int32, ctypes.c_int64, P, P, ctypes.c_int32, P,
-                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, P, P, P, P,
+                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, P, P, P, P, P, P, P,
                                     ctypes.c_int32]
         L.oracle_render.restype = ctypes.c_int
         _lib = L
@@ -124,13 +125,19 @@ class OracleScene:
 
     def render(self, cameras, poses: np.ndarray, step: int, rays: np.ndarray, sensor=None, step0: int = 0,
                s_first: Optional[np.ndarray] = None, env_offset: int = 0,
-               per_env_intrinsics: Optional[np.ndarray] = None, flags: bool = True, threads: int = 0):
+               per_env_intrinsics: Optional[np.ndarray] = None, flags: bool = True, threads: int = 0,
+               mount_dr: Optional[np.ndarray] = None, rsm_mode: Optional[np.ndarray] = None,
+               rsm_cols: Sequence[int] = (0, 0, 0)):
         """Depth of the rays [N,4] = (env, cam, x, y) at `step`; poses [S,E,L,7] start at step0.
+        (x, y) index the output image ((width, height) / downsample).  mount_dr [E,C,7] perturbs each
+        env's camera mounts (dp xyz, dq xyzw); rsm_mode [E] (0 none, 1 small, 2 large) with rsm_cols
+        masks that many columns on both sides of every image.
 
         Returns dict(depth=[N] f64, raw=[N] f64, k=[N] i32, flags=[N] i32)."""
         poses = np.ascontiguousarray(poses, np.float32)
         S, E, L, _ = poses.shape
-        cam_i = np.ascontiguousarray([[c.width, c.height, c.mount_link] for c in cameras], np.int32)
+        cam_i = np.ascontiguousarray([[c.width, c.height, c.mount_link, getattr(c, "downsample", 1)]
+                                      for c in cameras], np.int32)
         cam_f = np.ascontiguousarray([[c.fx, c.fy, c.cx, c.cy, *c.offset_pos, *c.offset_quat, c.d_min, c.d_max]
                                       for c in cameras], np.float32)
         rays = np.ascontiguousarray(rays, np.int64).reshape(-1, 4)
@@ -144,25 +151,30 @@ class OracleScene:
             sen.depth_kind = sensor.depth_kind
         sf = None if s_first is None else np.ascontiguousarray(s_first, np.int64)
         intr = None if per_env_intrinsics is None else np.ascontiguousarray(per_env_intrinsics, np.float32)
+        mdr = None if mount_dr is None else np.ascontiguousarray(mount_dr, np.float32).reshape(E, len(cameras), 7)
+        rsm = None if rsm_mode is None else np.ascontiguousarray(rsm_mode, np.uint8).reshape(E)
+        cols = np.ascontiguousarray(rsm_cols, np.int32).reshape(3)
         depth = np.zeros(n, np.float64)
         raw = np.zeros(n, np.float64)
         k = np.zeros(n, np.int32)
         fl = np.zeros(n, np.int32)
         rc = lib().oracle_render(self._h, _ptr(cam_i), _ptr(cam_f), len(cameras), _ptr(intr), _ptr(poses), S, E, L,
                                  int(step0), _ptr(sf), ctypes.byref(sen), int(env_offset), _ptr(rays), n,
-                                 int(step), int(bool(flags)), _ptr(depth), _ptr(raw), _ptr(k), _ptr(fl),
-                                 int(threads))
+                                 int(step), int(bool(flags)), _ptr(mdr), _ptr(rsm), _ptr(cols), _ptr(depth),
+                                 _ptr(raw), _ptr(k), _ptr(fl), int(threads))
         if rc != 0:
-            raise ValueError("oracle_render: bad argument (ray index, step outside the pose window, s_first)")
+            raise ValueError("oracle_render: bad argument (ray index, step outside the pose window, s_first, "
+                         "a downsample factor that does not divide the image)")
         return {"depth": depth, "raw": raw, "k": k, "flags": fl}
 
 
 def all_rays(cameras, n_envs: int) -> np.ndarray:
-    """Every (env, cam, x, y) in the packed output order [E][cam][y][x]."""
+    """Every (env, cam, x, y) of the output images in the packed order [E][cam][y][x]."""
     out = []
     for e in range(n_envs):
         for c, cam in enumerate(cameras):
-            y, x = np.meshgrid(np.arange(cam.height), np.arange(cam.width), indexing="ij")
+            f = getattr(cam, "downsample", 1)
+            y, x = np.meshgrid(np.arange(cam.height // f), np.arange(cam.width // f), indexing="ij")
             n = x.size
             out.append(np.stack([np.full(n, e), np.full(n, c), x.reshape(-1), y.reshape(-1)], axis=1))
     return np.concatenate(out).astype(np.int64)

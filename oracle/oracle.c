@@ -5,7 +5,7 @@
  * Only the tests, the package smoke check and the benchmark's CPU-baseline leg build, load or call
  * it; the product path never links it and shares no code, header, table or helper with it.
  *
- * What it computes (Sec. 3.2.1 "Efficient Multi-Depth System Simulation", Algorithm 1, and the
+ * What it computes (Sec. 3.2.2 "Efficient Multi-Depth System Simulation", Algorithm 1, and the
  * perception rows of the domain-randomisation table in Appendix A.2):
  *   for every requested (env e, camera c, pixel x, y) at step s:
  *     1. camera pose   : link pose (t_l, q_l) of the mounting link composed with the mount offset;
@@ -13,10 +13,19 @@
  *                        y down, z forward), d = R_c r / |r|, o = p_c, m = 1/|r|          (Alg. 1)
  *     3. closest hit   : every triangle of env e's link meshes (placed in the world by the link
  *                        poses) and every triangle of the shared terrain, intersected in FP64,
- *                        z_raw = min(d_max, min over hits of m*t)          (Alg. 1, far plane Sec. 3.2.1)
- *     4. sensor        : latency k ~ U{0..Lmax} per (env, camera, step); source step
+ *                        z_raw = min(d_max, min over hits of m*t)          (Alg. 1, far plane Sec. 3.2.2)
+ *     4. downsample    : a camera rendered at raw resolution W x H and downsampled by f gives the
+ *                        (W/f) x (H/f) image whose pixel is the mean of its f x f raw block
+ *                        (240x135 raw to 48x27, Sec. 4.1, perception settings)
+ *     5. sensor        : latency k ~ U{0..Lmax} per (env, camera, step); source step
  *                        s' = max(s - k, s_first[e]); z = z_raw(s'); Gaussian noise on hits,
  *                        clip to [d_min, d_max], pixel dropout                   (Appendix A.2)
+ *     6. side masking  : an env in mask mode 1 (small) or 2 (large) has the outer n_mode columns on
+ *                        both sides of every image filled with uniform values in [d_min, d_max]
+ *                        (Random Side Masking, Sec. 3.2.4)
+ *   Camera randomisation (Appendix A.2, perception rows): the mount of camera c in env e may be
+ *   perturbed per env by (dp, dq): offset p_off + dp in the link frame, rotation R(q_off) R(dq), so
+ *   dq rotates about the camera's own axes; FOV randomisation is per-env intrinsics.
  *   Random words come from Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by
  *   (global env, camera, pixel, step).
  *
@@ -28,7 +37,12 @@
  *   - n = sqrt(-2 ln u1) cos(2 pi u2), u1 = (w1 + 1) 2^-32, u2 = w2 2^-32 (Box-Muller);
  *   - dropout after clipping: if w0 < floor(p 2^32) the pixel becomes `fill`;
  *   - latency word: Philox with pixel field 0xFFFFFFFF, k = (w0 * (Lmax + 1)) >> 32;
- *   - counter (ge, c, pixel, step_lo), key (seed0 ^ step_hi, seed1).
+ *   - counter (ge, c, pixel, step_lo), key (seed0 ^ step_hi, seed1); the pixel index is that of
+ *     the output (downsampled) image;
+ *   - downsampling is the plain mean of the f x f raw depths (misses count as d_max), taken before
+ *     the sensor model, so the latency ring and the noise act on the policy-resolution image;
+ *   - side-mask fill: d_min + (d_max - d_min) (w3 + 1/2) 2^-32 with w3 the fourth word of the keyed
+ *     stream at the current step s (not the source step), applied after dropout.
  *
  * Besides the depth, each ray gets flags that say where FP32 arithmetic may legitimately decide
  * differently: the ray passes within eps of a silhouette edge (boundary edge or crease) of a
@@ -384,7 +398,7 @@ static void mesh_silhouette(const mesh_t *m, const double *R, vec3 tr, const ray
 /* ---------------------------------------------------------------------------------------------
  * Cameras and sensor
  * ------------------------------------------------------------------------------------------- */
-/* cam_i [C,3] = (width, height, mount_link);
+/* cam_i [C,4] = (raw width, raw height, mount_link, downsample factor f >= 1);
  * cam_f [C,13] = (fx, fy, cx, cy, off_x, off_y, off_z, q_x, q_y, q_z, q_w, d_min, d_max). */
 typedef struct {
     float sigma_abs, sigma_rel, p_drop, fill;
@@ -400,12 +414,14 @@ enum {
     ORACLE_FLAG_DROPPED = 8,     /* dropout replaced the pixel by `fill` */
     ORACLE_FLAG_GRAZING = 16,    /* the visible hit is so oblique that FP32 rounding of the ray alone can
                                     move the depth by more than 2.5e-5 m (a quarter of the tolerance) */
+    ORACLE_FLAG_MASKED = 32,     /* side masking replaced the pixel by a uniform value */
 };
 
 /* Raw depth of one pixel from the poses of one step; fills flags bits 0..2 when want_flags. */
 static double raw_depth(const oracle_scene *S, const int32_t *cam_i, const float *cam_f, int32_t C,
-                        const float *intr_env, const float *poses_step, int32_t L, int32_t e,
-                        int32_t c, int32_t x, int32_t y, int32_t depth_kind, int want_flags, int *flags)
+                        const float *intr_env, const float *mount_dr, const float *poses_step, int32_t L,
+                        int32_t e, int32_t c, int32_t x, int32_t y, int32_t depth_kind, int want_flags,
+                        int *flags)
 {
     const float *cf = cam_f + 13 * c;
     double fx = cf[0], fy = cf[1], cx = cf[2], cy = cf[3];
@@ -414,15 +430,25 @@ static double raw_depth(const oracle_scene *S, const int32_t *cam_i, const float
         fx = k[0]; fy = k[1]; cx = k[2]; cy = k[3];
     }
     double d_max = cf[12];
-    int32_t mount = cam_i[3 * c + 2];
+    int32_t mount = cam_i[4 * c + 2];
 
     /* 1. camera pose = mounting link pose composed with the mount offset */
     const float *lp = poses_step + 7 * ((int64_t)e * L + mount);
     double Rl[9], Roff[9], Rc[9];
     quat_to_mat(lp + 3, Rl);
     quat_to_mat(cf + 7, Roff);
+    vec3 p_off = v3(cf[4], cf[5], cf[6]);
+    if (mount_dr) {
+        /* randomised mount: offset p_off + dp, rotation R(q_off) R(dq) */
+        const float *dr = mount_dr + 7 * ((int64_t)e * C + c);
+        double Rdq[9], Rm[9];
+        quat_to_mat(dr + 3, Rdq);
+        mat_mul(Roff, Rdq, Rm);
+        memcpy(Roff, Rm, sizeof Rm);
+        p_off = vadd(p_off, v3(dr[0], dr[1], dr[2]));
+    }
     mat_mul(Rl, Roff, Rc);
-    vec3 p_c = vadd(v3(lp[0], lp[1], lp[2]), mat_vec(Rl, v3(cf[4], cf[5], cf[6])));
+    vec3 p_c = vadd(v3(lp[0], lp[1], lp[2]), mat_vec(Rl, p_off));
 
     /* 2. BuildDepthRay */
     vec3 r = v3((x - cx) / fx, (y - cy) / fy, 1.0);
@@ -472,11 +498,33 @@ static double raw_depth(const oracle_scene *S, const int32_t *cam_i, const float
     return z;
 }
 
+/* Depth of output pixel (x, y) of camera c before the sensor: the raw depth when the camera is not
+ * downsampled, else the mean of the f x f raw pixels (f x + i, f y + j); flags are OR-ed. */
+static double image_depth(const oracle_scene *S, const int32_t *cam_i, const float *cam_f, int32_t C,
+                          const float *intr_env, const float *mount_dr, const float *poses_step, int32_t L,
+                          int32_t e, int32_t c, int32_t x, int32_t y, int32_t depth_kind, int want_flags,
+                          int *flags)
+{
+    int32_t f = cam_i[4 * c + 3];
+    if (f <= 1)
+        return raw_depth(S, cam_i, cam_f, C, intr_env, mount_dr, poses_step, L, e, c, x, y, depth_kind,
+                         want_flags, flags);
+    double sum = 0.0;
+    for (int32_t j = 0; j < f; ++j)
+        for (int32_t i = 0; i < f; ++i)
+            sum += raw_depth(S, cam_i, cam_f, C, intr_env, mount_dr, poses_step, L, e, c, f * x + i, f * y + j,
+                             depth_kind, want_flags, flags);
+    return sum / ((double)f * (double)f);
+}
+
 /*
  * Render the requested rays at step `step`.
  *   poses     [S,E,L,7] float32, poses[i] belongs to step step0 + i
  *   s_first   [E] first step of each env since its reset (NULL: all step0)
- *   rays      [N,4] int64 (e, c, x, y)
+ *   rays      [N,4] int64 (e, c, x, y), (x, y) a pixel of the output (downsampled) image
+ *   mount_dr  [E,C,7] float32 per-env mount perturbation (dp xyz, dq xyzw) or NULL
+ *   rsm_mode  [E] uint8 side-mask mode (0 none, 1 small, 2 large; larger values count as 2) or NULL
+ *   rsm_cols  [3] columns masked on each side for modes 0, 1, 2 (ignored when rsm_mode is NULL)
  *   outputs   depth [N] (sensor applied), raw [N] (z_raw of the source step), k [N], flags [N]
  * Returns 0, or -1 for a bad argument (a source step without poses, an index out of range).
  */
@@ -485,14 +533,20 @@ ORACLE_EXPORT int oracle_render(const oracle_scene *S, const int32_t *cam_i, con
                                 int64_t n_steps, int32_t n_envs, int32_t n_links, int64_t step0,
                                 const int64_t *s_first, const oracle_sensor *sensor, int32_t env_offset,
                                 const int64_t *rays, int64_t n_rays, int64_t step, int32_t want_flags,
+                                const float *mount_dr, const uint8_t *rsm_mode, const int32_t *rsm_cols,
                                 double *depth, double *raw, int32_t *k_out, int32_t *flags_out,
                                 int32_t n_threads)
 {
+    for (int32_t c = 0; c < n_cams; ++c) {
+        int32_t f = cam_i[4 * c + 3];
+        if (f < 1 || cam_i[4 * c] % f != 0 || cam_i[4 * c + 1] % f != 0) return -1;
+    }
     for (int64_t i = 0; i < n_rays; ++i) {
         const int64_t *q = rays + 4 * i;
         if (q[0] < 0 || q[0] >= n_envs || q[1] < 0 || q[1] >= n_cams) return -1;
-        if (q[2] < 0 || q[2] >= cam_i[3 * q[1]] || q[3] < 0 || q[3] >= cam_i[3 * q[1] + 1]) return -1;
-        if (cam_i[3 * q[1] + 2] < 0 || cam_i[3 * q[1] + 2] >= n_links) return -1;
+        const int32_t *ci = cam_i + 4 * q[1];
+        if (q[2] < 0 || q[2] >= ci[0] / ci[3] || q[3] < 0 || q[3] >= ci[1] / ci[3]) return -1;
+        if (ci[2] < 0 || ci[2] >= n_links) return -1;
     }
     if (step < step0 || step >= step0 + n_steps) return -1;
     for (int32_t e = 0; e < n_envs; ++e)
@@ -514,7 +568,7 @@ ORACLE_EXPORT int oracle_render(const oracle_scene *S, const int32_t *cam_i, con
     for (int64_t i = 0; i < n_rays; ++i) {
         const int64_t *q = rays + 4 * i;
         int32_t e = (int32_t)q[0], c = (int32_t)q[1], x = (int32_t)q[2], y = (int32_t)q[3];
-        int32_t W = cam_i[3 * c];
+        int32_t W = cam_i[4 * c] / cam_i[4 * c + 3];   /* output width */
         const float *cf = cam_f + 13 * c;
         double d_min = cf[11], d_max = cf[12];
         uint32_t ge = (uint32_t)(env_offset + e);
@@ -529,8 +583,8 @@ ORACLE_EXPORT int oracle_render(const oracle_scene *S, const int32_t *cam_i, con
         if (src < step0) { err = 1; continue; }
 
         int flags = 0;
-        double zr = raw_depth(S, cam_i, cam_f, n_cams, intr_env, poses + (src - step0) * stride, n_links,
-                              e, c, x, y, sensor->depth_kind, want_flags, &flags);
+        double zr = image_depth(S, cam_i, cam_f, n_cams, intr_env, mount_dr, poses + (src - step0) * stride,
+                                n_links, e, c, x, y, sensor->depth_kind, want_flags, &flags);
 
         /* noise, clip and dropout keyed by the source step */
         keyed_words(ge, (uint32_t)c, (uint32_t)(y * W + x), src, sensor->seed, w);
@@ -546,6 +600,16 @@ ORACLE_EXPORT int oracle_render(const oracle_scene *S, const int32_t *cam_i, con
         if ((uint64_t)w[0] < drop_thr) {
             z = sensor->fill;
             flags |= ORACLE_FLAG_DROPPED;
+        }
+        if (rsm_mode) {
+            /* side masking: the outer n columns on both sides, n by the env's mode */
+            int32_t mode = rsm_mode[e] > 2 ? 2 : rsm_mode[e];
+            int32_t n = rsm_cols[mode];
+            if (x < n || x >= W - n) {
+                keyed_words(ge, (uint32_t)c, (uint32_t)(y * W + x), step, sensor->seed, w);
+                z = d_min + (d_max - d_min) * (((double)w[3] + 0.5) * (1.0 / 4294967296.0));
+                flags |= ORACLE_FLAG_MASKED;
+            }
         }
         depth[i] = z;
         if (raw) raw[i] = zr;

@@ -1,4 +1,4 @@
-"""GB300-native multi-depth ray casting with a depth-sensor model (RPL, Sec. 3.2.1, Algorithm 1).
+"""GB300-native multi-depth ray casting with a depth-sensor model (RPL, Sec. 3.2.2, Algorithm 1).
 
 Submodules:
   rpl        ctypes binding of librpl.so (same names as include/rpl.h) plus Scene / View owners

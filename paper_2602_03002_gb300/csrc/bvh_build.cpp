@@ -1,6 +1,6 @@
 // bvh_build.cpp -- one-time host build of the terrain and link BVHs (binned SAH, multithreaded).
 //
-// Sec. 3.2.1 keeps every mesh static in its own frame so that no acceleration structure is refitted
+// Sec. 3.2.2 keeps every mesh static in its own frame so that no acceleration structure is refitted
 // per frame; the BVHs are therefore built once on the host, with care for quality (SAH), and
 // uploaded.  The top levels are split on the calling thread (with the binning of large ranges
 // spread over threads); the remaining subtrees are built by a pool of threads into private node

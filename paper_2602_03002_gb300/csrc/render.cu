@@ -1,4 +1,4 @@
-// render.cu -- sm_103a kernels of the multi-depth ray-casting path (Sec. 3.2.1, Algorithm 1) and of
+// render.cu -- sm_103a kernels of the multi-depth ray-casting path (Sec. 3.2.2, Algorithm 1) and of
 // the depth-sensor model (Appendix A.2).
 //
 //   prep_kernel    one thread per (env, link): normalised link rotation, world->link transform and

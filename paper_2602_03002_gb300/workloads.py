@@ -1,4 +1,4 @@
-"""Seeded synthetic inputs for multi-depth ray casting (Sec. 3.2.1, Algorithm 1).
+"""Seeded synthetic inputs for multi-depth ray casting (Sec. 3.2.2, Algorithm 1).
 
 This module builds the *inputs* of the method and nothing else: terrain heightfield meshes in the
 paper's terrain families (20 deg slopes, stairs with 0.22/0.25/0.30 m runs, 0.25 m stepping stones
@@ -47,6 +47,15 @@ class Camera:
     offset_quat: Tuple[float, float, float, float]  # xyzw, optical frame -> link frame
     d_min: float
     d_max: float
+    downsample: int = 1   # f: rendered at width x height, output (width / f) x (height / f)
+
+    @property
+    def out_width(self) -> int:
+        return self.width // max(1, self.downsample)
+
+    @property
+    def out_height(self) -> int:
+        return self.height // max(1, self.downsample)
 
 
 @dataclasses.dataclass

@@ -424,3 +424,99 @@ def test_latency_identity_exact():
             sl = slice(e * npx, (e + 1) * npx)
             assert np.array_equal(fd["depth"][sl], fs["depth"][sl]), (s, e, k)
             assert np.all(fd["k"][sl] == k)                    # one draw per (env, camera, step)
+
+
+# --------------------------------------------------------------------------------------------------
+# adjacent steps: downsampling, randomised camera mounts, side masking
+# --------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("f", [2, 5])
+def test_downsample_is_the_block_mean_of_the_raw_closed_form(f):
+    """A camera rendered at W x H and downsampled by f: every output pixel is the mean of its f x f
+    raw block.  Expected values: the plane closed form per raw pixel, reshaped and averaged by numpy
+    (a transposed block index or a dropped row of the block fails this: the image is yawed and
+    partly beyond the far plane, so depth varies along both axes and includes misses)."""
+    h, Hc = 0.0, 1.3
+    cam = _cam(8 * f, 5 * f, 90.0, 60.0, 25.0, 30.0)
+    cam.downsample = f
+    q = Rotation.from_euler("z", 40.0, degrees=True).as_quat()
+    out = _render(_plane_mesh(h), [EMPTY], [cam], _pose((0.2, 0.1, Hc), q)[None, None])
+    right, down, fwd = _axes_world(cam, q)
+    D, _ = _pixel_dirs(cam, right, down, fwd)
+    lam = np.where(D[:, 2] < 0, (_f32(h) - _f32(Hc)) / np.where(D[:, 2] < 0, D[:, 2], -1.0), np.inf)
+    raw = np.where(np.isfinite(lam) & (lam > 0) & (lam < cam.d_max), lam, cam.d_max).reshape(cam.height, cam.width)
+    want = raw.reshape(cam.height // f, f, cam.width // f, f).mean(axis=(1, 3))
+    want = np.clip(want, cam.d_min, cam.d_max)
+    assert out["depth"].shape == (cam.out_width * cam.out_height,)
+    np.testing.assert_allclose(out["depth"], want.reshape(-1), rtol=0, atol=1e-9)
+    assert (want < cam.d_max).any() and (want == cam.d_max).any() and (raw[:, 0] != raw[:, -1]).any()
+
+
+def test_downsample_factor_must_divide_the_image():
+    cam = _cam(10, 6, 90.0, 60.0, 0.0, 30.0)
+    cam.downsample = 4
+    with pytest.raises(ValueError):
+        _render(_plane_mesh(0.0), [EMPTY], [cam], _pose((0, 0, 1.0))[None, None], rays=np.zeros((1, 4), np.int64))
+
+
+def test_randomised_mounts_plane_closed_form():
+    """Per-env mount perturbation (dp, dq): camera at t_l + R_l (p_off + dp) with rotation
+    R_l R_off R_dq (dq about the camera's own axes), checked against the plane closed form with the
+    rotations composed by scipy."""
+    rng = np.random.default_rng(3)
+    h, E = 0.1, 5
+    cam = _cam(12, 9, 80.0, 55.0, 10.0, 40.0, pos=(0.1, 0.0, 0.3))
+    euler = np.stack([rng.uniform(-2.5, 2.5, E), rng.uniform(-3.0, 3.0, E), rng.uniform(-2.5, 2.5, E)], 1)
+    dq = Rotation.from_euler("xyz", euler, degrees=True).as_quat()
+    dp = rng.uniform(-0.025, 0.025, (E, 3))
+    mount_dr = np.concatenate([dp, dq], 1).astype(np.float32)[:, None, :]        # [E, C=1, 7]
+    link_q = Rotation.from_euler("z", rng.uniform(-180, 180, (E, 1)), degrees=True).as_quat()
+    poses = np.stack([_pose((3.0 * e, 0.5, 1.2), link_q[e]) for e in range(E)])[:, None, :]
+    out = _render(_plane_mesh(h, half=60.0), [EMPTY], [cam], poses, mount_dr=mount_dr)
+    npx = cam.width * cam.height
+    for e in range(E):
+        Rl = Rotation.from_quat(_f32(link_q[e])).as_matrix()
+        R = Rl @ Rotation.from_quat(_f32(cam.offset_quat)).as_matrix() @ Rotation.from_quat(_f32(dq[e])).as_matrix()
+        o = _f32((3.0 * e, 0.5, 1.2)) + Rl @ (_f32(cam.offset_pos) + _f32(dp[e]))
+        D, _ = _pixel_dirs(cam, R[:, 0], R[:, 1], R[:, 2])
+        lam = np.where(D[:, 2] < 0, (_f32(h) - o[2]) / np.where(D[:, 2] < 0, D[:, 2], -1.0), np.inf)
+        np.testing.assert_allclose(out["depth"][e * npx:(e + 1) * npx], _clipped(lam, cam), rtol=0, atol=1e-9)
+    # the perturbation matters: without it the depths differ
+    plain = _render(_plane_mesh(h, half=60.0), [EMPTY], [cam], poses)
+    assert np.abs(plain["depth"] - out["depth"]).max() > 1e-3
+
+
+def test_side_masking_columns_values_and_key():
+    """Modes 0/1/2 mask 0/n1/n2 columns on both sides; the rest of the image is untouched; a masked
+    value is d_min + (d_max - d_min)(w3 + 1/2) 2^-32 from the keyed stream of the current step (not
+    the latency's source step); the values are uniform on [d_min, d_max]."""
+    sen = W.Sensor(sigma_abs=0.01, p_drop=0.05, max_latency=3, seed=(21, 22))
+    cam = _cam(24, 10, 80.0, 60.0, 0.0, 50.0)
+    E, S, step, env_offset = 4, 6, 5, 7
+    modes = np.array([0, 1, 2, 1], np.uint8)
+    cols = (0, 3, 7)
+    poses = np.stack([np.stack([_pose((e * 3.0, 0, 1.2 + 0.03 * e))]) for e in range(E)])
+    poses = np.repeat(poses[None], S, axis=0)
+    for s in range(S):
+        poses[s, :, 0, 2] += 0.04 * s
+    sc = oracle.OracleScene(*_plane_mesh(0.0), [EMPTY[0]], [EMPTY[1]])
+    rays = oracle.all_rays([cam], E)
+    base = sc.render([cam], poses, step, rays, sen, env_offset=env_offset)
+    m = sc.render([cam], poses, step, rays, sen, env_offset=env_offset, rsm_mode=modes, rsm_cols=cols)
+    assert (base["k"] > 0).any()                                # some sources are earlier steps
+    x = rays[:, 2]
+    n = np.asarray(cols)[modes[rays[:, 0]]]
+    masked = (x < n) | (x >= cam.width - n)
+    assert np.array_equal((m["flags"] & oracle.FLAG_MASKED) != 0, masked)
+    assert np.array_equal(m["depth"][~masked], base["depth"][~masked])
+    for i in np.flatnonzero(masked)[::5]:
+        e, c, xx, yy = rays[i]
+        w = oracle.philox4x32_10([env_offset + e, c, yy * cam.width + xx, step], [sen.seed[0], sen.seed[1]])
+        want = np.float64(np.float32(cam.d_min)) + (np.float64(np.float32(cam.d_max)) - np.float64(np.float32(cam.d_min))) \
+            * ((float(w[3]) + 0.5) / 2.0 ** 32)
+        assert m["depth"][i] == want
+    # uniformity of the fill over many masked pixels
+    big = _cam(64, 48, 80.0, 60.0, 0.0, 50.0)
+    r = oracle.all_rays([big], E)
+    mm = sc.render([big], poses, step, r, sen, rsm_mode=np.full(E, 2, np.uint8), rsm_cols=(0, 0, 32), flags=False)
+    u = (mm["depth"] - np.float32(big.d_min)) / (np.float32(big.d_max) - np.float32(big.d_min))
+    assert stats.kstest(u, "uniform").pvalue > 1e-4
