@@ -219,7 +219,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt_tot / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(w, args.variant)},
-            "frames_per_s": rate / (w.pixels_per_env / len(w.cameras)),
+            "frames_per_s": rate / (w.raw_pixels_per_env / len(w.cameras)),
             "e2e": {"value": rate / 1e9, "unit": "Grays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "cpu_baseline": {"value": rate / 1e9, "unit": "Grays/s", "cores": cores, "kind": "oracle",
                              "sample": sample}}

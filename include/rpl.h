@@ -82,7 +82,11 @@ typedef struct {
 /* Pinhole camera.  Pixel (x, y), 0 <= x < width, 0 <= y < height, has the camera-frame ray
  * r = ((x - cx)/fx, (y - cy)/fy, 1) (Sec. 3.2.2: r_c = K^-1 [x, y, 1]^T).  The camera pose is the
  * pose of link `mount_link` composed with (offset_pos, offset_quat_xyzw).  Depths are clipped to
- * [d_min, d_max]; a ray that hits nothing closer than d_max reports d_max (the far plane). */
+ * [d_min, d_max]; a ray that hits nothing closer than d_max reports d_max (the far plane).
+ * downsample f (0 or 1: none; else 2..16 dividing width and height): the camera is ray cast at
+ * width x height and its output image is (width/f) x (height/f), each pixel the mean of its f x f
+ * block of raw depths (misses count as d_max), taken before the sensor model (Sec. 4.1: raw
+ * 240x135 downsampled to 48x27).  The intrinsics are those of the raw image. */
 typedef struct {
     int32_t width, height;
     float fx, fy, cx, cy;
@@ -90,6 +94,7 @@ typedef struct {
     float offset_pos[3];
     float offset_quat_xyzw[4];
     float d_min, d_max;
+    int32_t downsample;
 } rpl_camera;
 
 /* Depth-sensor model (Appendix A.2: process delay, noise, dropout).  For output step s, pixel p
@@ -182,10 +187,32 @@ RPL_API rpl_status rpl_view_create(rpl_scene_t scene, int32_t n_envs, int32_t n_
 /* Set the cameras (1..RPL_MAX_CAMERAS; they may differ in size).  per_env_intrinsics, host or
  * device, is NULL or [n_envs, n_cams, 4] float32 (fx, fy, cx, cy) overriding each camera's
  * intrinsics per env (Sec. 3.2.2: batched inverse intrinsics for per-env FOV randomisation).
- * Restarts the sensor state (as rpl_view_reset with no mask).  Errors: INVALID_ARG (size <= 0,
- * fx or fy == 0, mount_link out of range, d_min > d_max), CAPACITY, OUT_OF_MEMORY. */
+ * Allocates the raw-depth buffer of downsampled cameras ([n_envs, raw pixels per env] float32)
+ * and clears the mount randomisation.  Restarts the sensor state (as rpl_view_reset with no
+ * mask).  Errors: INVALID_ARG (size <= 0, fx or fy == 0, mount_link out of range, d_min > d_max,
+ * a downsample factor outside 0..16 or not dividing the size), CAPACITY, OUT_OF_MEMORY. */
 RPL_API rpl_status rpl_cameras_set(rpl_view_t view, const rpl_camera *cams, int32_t n_cams,
                                    const float *per_env_intrinsics);
+
+/* Per-env camera mount randomisation (Appendix A.2, perception rows: camera translation and
+ * rotation).  mount_delta, host or device, is [n_envs, n_cams, 7] float32 (dp_x, dp_y, dp_z, dq_x,
+ * dq_y, dq_z, dq_w): camera c of env e is mounted at offset_pos + dp (link frame) with rotation
+ * R(offset_quat) R(dq), i.e. dq turns the camera about its own axes; dq is normalised.  The values
+ * are copied (call again to re-draw them, e.g. at episode resets); NULL restores the plain mounts.
+ * FOV randomisation is the per-env intrinsics of rpl_cameras_set.  Call after rpl_cameras_set
+ * (which clears them).  Does not restart the sensor state.  Errors: INVALID_ARG (no cameras set,
+ * a zero or non-finite quaternion), OUT_OF_MEMORY, CUDA. */
+RPL_API rpl_status rpl_cameras_randomize(rpl_view_t view, const float *mount_delta);
+
+/* Random Side Masking (Sec. 3.2.4).  env_mode, host or device, is NULL (masking off) or [n_envs]
+ * uint8: 0 none, 1 small, 2 large (larger values count as 2); cols[m] is the number of output
+ * columns masked on each side of every image of an env in mode m (0 <= cols[m], 2 cols[m] may
+ * cover the whole width).  A masked pixel of camera c in global env g at step s is replaced, after
+ * the rest of the sensor model, by d_min + (d_max - d_min) (w3(g, c, p, s) + 1/2) 2^-32, a uniform
+ * value in [d_min, d_max] keyed by the current step (not the latency's source step).  The modes are
+ * copied; call again when they change.  Errors: INVALID_ARG (negative cols, cols NULL with env_mode
+ * set), OUT_OF_MEMORY, CUDA. */
+RPL_API rpl_status rpl_side_mask_set(rpl_view_t view, const int32_t cols[3], const uint8_t *env_mode);
 
 /* Set the sensor model (see rpl_sensor_params).  Allocates the latency ring buffer,
  * [n_envs, max_latency + 1, pixels per env] float32, and restarts the sensor state.
@@ -368,8 +395,8 @@ RPL_API void rpl_view_destroy(rpl_view_t view);
  * array and it keeps the last call's contents: each call rewrites all of it that it reads, and
  * clears its error word, but calls whose work overlaps on the GPU (other streams, other threads)
  * race on it and must be serialised by the caller.  The call only enqueues work.
- * Errors: INVALID_ARG (unfrozen scene, bad counts, cameras or sensor, max_latency != 0), CAPACITY,
- * CUDA. */
+ * Errors: INVALID_ARG (unfrozen scene, bad counts, cameras or sensor, max_latency != 0, a camera
+ * with downsample > 1, whose raw image needs a view's buffer), CAPACITY, CUDA. */
 RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const rpl_camera *cams, int32_t n_cams,
                                              int32_t n_envs, int32_t n_links, const float *link_poses,
                                              const rpl_sensor_params *sensor, int64_t step,

@@ -95,9 +95,16 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
             !(k.fy != 0.f) || k.mount_link < 0 || k.mount_link >= n_links || !(k.d_min <= k.d_max) ||
             !(k.d_max > 0.f))
             return set_error(RPL_ERR_INVALID_ARG, "rpl_render_static_scratch: bad camera");
+        if (k.downsample > 1)
+            return set_error(RPL_ERR_INVALID_ARG, "rpl_render_static_scratch: a downsampled camera needs a view's "
+                                                  "raw-depth buffer");
         CamDev &d = cd[c];
         d.width = k.width;
         d.height = k.height;
+        d.ds = 1;
+        d.out_w = k.width;
+        d.out_h = k.height;
+        d.raw_off = 0;
         d.tiles_x = (k.width + 7) / 8;
         d.tile_off = tiles;
         d.pix_off = (int32_t)pix;

@@ -3,12 +3,15 @@
 //
 //   prep_kernel    one thread per (env, link): normalised link rotation, world->link transform and
 //                  the link's world AABB; one thread per (env, camera): camera pose = link pose
-//                  composed with the mount offset.
-//   render_kernel  one thread per pixel ray, one warp per 8x4 pixel tile of one (env, camera):
+//                  composed with the (optionally per-env randomised) mount offset.
+//   render_kernel  one thread per pixel ray, one warp per 32-pixel tile of one (env, camera):
 //                  BuildDepthRay -> links whose world AABB the ray meets within the running bound
 //                  (ray moved into the link frame, link BVH traversed, bound shrinks on each hit)
 //                  -> terrain BVH traversal with the bound -> far-plane clip -> fused sensor model
-//                  (ring-buffer write, latency select, noise, clip, dropout) -> store.
+//                  (ring-buffer write, latency select, noise, clip, dropout, side mask) -> store;
+//                  rays of a downsampled camera store their raw depth instead.
+//   downsample_kernel  one thread per output pixel of a downsampled camera: mean of its raw block
+//                  -> the same sensor epilogue -> store.
 //
 // The path is pointer chasing, not a dense contraction, so it runs on the SIMT pipes: node and
 // triangle fetches are 16-byte read-only vector loads, the per-ray stack is short, rays of a warp
@@ -141,15 +144,32 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
     float Rl[9], Ro[9];
     quat_rot(q[3], q[4], q[5], q[6], Rl);
     quat_rot(cam.off_quat[0], cam.off_quat[1], cam.off_quat[2], cam.off_quat[3], Ro);
+    float op[3] = {cam.off_pos[0], cam.off_pos[1], cam.off_pos[2]};
+    if (p.mount_dr) {
+        // randomised mount of this env: offset + dp, rotation R_off R(dq) (dq about the camera's axes)
+        const float *dr = p.mount_dr + 7 * j;
+        float Rd[9], Rm[9];
+        quat_rot(dr[3], dr[4], dr[5], dr[6], Rd);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                Rm[3 * r + k] = Ro[3 * r + 0] * Rd[k] + Ro[3 * r + 1] * Rd[3 + k] + Ro[3 * r + 2] * Rd[6 + k];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Ro[k] = Rm[k];
+        op[0] += dr[0];
+        op[1] += dr[1];
+        op[2] += dr[2];
+    }
     float Rc[9];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int k = 0; k < 3; ++k)
             Rc[3 * r + k] = Rl[3 * r + 0] * Ro[k] + Rl[3 * r + 1] * Ro[3 + k] + Rl[3 * r + 2] * Ro[6 + k];
-    const float ox = Rl[0] * cam.off_pos[0] + Rl[1] * cam.off_pos[1] + Rl[2] * cam.off_pos[2];
-    const float oy = Rl[3] * cam.off_pos[0] + Rl[4] * cam.off_pos[1] + Rl[5] * cam.off_pos[2];
-    const float oz = Rl[6] * cam.off_pos[0] + Rl[7] * cam.off_pos[1] + Rl[8] * cam.off_pos[2];
+    const float ox = Rl[0] * op[0] + Rl[1] * op[1] + Rl[2] * op[2];
+    const float oy = Rl[3] * op[0] + Rl[4] * op[1] + Rl[5] * op[2];
+    const float oz = Rl[6] * op[0] + Rl[7] * op[1] + Rl[8] * op[2];
     p.cam_xf[5 * j + 0] = make_float4(Rc[0], Rc[1], Rc[2], q[0]);
     p.cam_xf[5 * j + 1] = make_float4(Rc[3], Rc[4], Rc[5], q[1]);
     p.cam_xf[5 * j + 2] = make_float4(Rc[6], Rc[7], Rc[8], q[2]);
@@ -590,6 +610,58 @@ __device__ __forceinline__ bool traverse8(const float4 *__restrict__ nodes, cons
 // One warp renders one tile of 32 pixel rays (tile_w x tile_h, tile_w = 2^tile_w_log2) of one
 // (env, camera).  Called once per warp, or in a grid-stride loop by the persistent launch; `warp` is
 // uniform across the warp so the warp-wide reductions below see all 32 lanes.
+// The sensor model and the store of output pixel (x, y) of camera c in env e, whose pre-sensor
+// depth at this step is z: ring-buffer write, latency select (source step = step - delta, drawn by
+// the prep kernel), noise on hits, clip, dropout, side mask (Appendix A.2; Sec. 3.2.4).
+__device__ __forceinline__ void finish_pixel(const RenderParams &p, int e, int c, const CamDev &cam, int x, int y,
+                                             float z, int64_t step, uint32_t delta) {
+    const uint32_t pix = (uint32_t)(y * cam.out_w + x);
+    const int64_t col = (int64_t)cam.pix_off + pix;
+    const uint32_t ge = p.env_offset + (uint32_t)e;
+    int64_t src = step;
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    if (p.sensor_on) {
+        const int64_t span = p.span;
+        if (span > 1) {
+            const int64_t slot = ((step % span) + span) % span;
+            p.ring[((int64_t)e * span + slot) * p.pix_per_env + col] = z;
+            src = step - (int64_t)delta;
+            if (src != step) {
+                const int64_t sslot = ((src % span) + span) % span;
+                z = p.ring[((int64_t)e * span + sslot) * p.pix_per_env + col];
+            }
+        }
+        w = sensor_words(ge, (uint32_t)c, pix, src, p.seed0, p.seed1);
+        if (z < cam.d_max) {
+            const float u1 = ((float)w.y + 1.0f) * 0x1p-32f;
+            const float u2 = (float)w.z * 0x1p-32f;
+            const float n = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+            z = z + (p.sigma_abs + p.sigma_rel * z) * n;
+        }
+        z = fminf(fmaxf(z, cam.d_min), cam.d_max);
+        if ((uint64_t)w.x < p.drop_thr) z = p.fill;
+    } else {
+        z = fminf(fmaxf(z, cam.d_min), cam.d_max);
+    }
+    if (p.rsm_mode) {
+        const int n = p.rsm_cols[min((int)p.rsm_mode[e], 2)];
+        if (x < n || x >= cam.out_w - n) {
+            // uniform fill keyed by the current step; the words above belong to the source step
+            if (!p.sensor_on || src != step) w = sensor_words(ge, (uint32_t)c, pix, step, p.seed0, p.seed1);
+            z = cam.d_min + (cam.d_max - cam.d_min) * (((float)w.w + 0.5f) * 0x1p-32f);
+        }
+    }
+    const int64_t o_idx = (int64_t)e * p.pix_per_env + col;
+    if (p.out_dtype == RPL_OUT_F32) {
+        static_cast<float *>(p.out)[o_idx] = z;
+    } else if (p.out_dtype == RPL_OUT_F16) {
+        static_cast<__half *>(p.out)[o_idx] = __float2half_rn(z);
+    } else {
+        const float q = rintf(fminf(fmaxf(z / cam.d_max, 0.f), 1.f) * 65535.f);
+        static_cast<uint16_t *>(p.out)[o_idx] = (uint16_t)q;
+    }
+}
+
 template <bool kCount, bool kWide>
 __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp, int lane, int64_t step) {
     const int e = (int)(warp / p.tiles_per_env);
@@ -710,43 +782,12 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
     }
     if (!ok) atomicOr(p.err, 1);
 
-    float z = hit ? fminf(m * tmax, cam.d_max) : cam.d_max;
-    const uint32_t pix = (uint32_t)(y * cam.width + x);
-    const int64_t col = (int64_t)cam.pix_off + pix;
-    if (p.sensor_on) {
-        const int64_t span = p.span;
-        const uint32_t ge = p.env_offset + (uint32_t)e;
-        int64_t src = step;
-        if (span > 1) {
-            const int64_t slot = ((step % span) + span) % span;
-            p.ring[((int64_t)e * span + slot) * p.pix_per_env + col] = z;
-            // the latency of this (env, camera, step) was drawn by the prep kernel: src = step - delta
-            src = step - (int64_t)__float_as_uint(CV.w);
-            if (src != step) {
-                const int64_t sslot = ((src % span) + span) % span;
-                z = p.ring[((int64_t)e * span + sslot) * p.pix_per_env + col];
-            }
-        }
-        const uint4 w = sensor_words(ge, (uint32_t)c, pix, src, p.seed0, p.seed1);
-        if (z < cam.d_max) {
-            const float u1 = ((float)w.y + 1.0f) * 0x1p-32f;
-            const float u2 = (float)w.z * 0x1p-32f;
-            const float n = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
-            z = z + (p.sigma_abs + p.sigma_rel * z) * n;
-        }
-        z = fminf(fmaxf(z, cam.d_min), cam.d_max);
-        if ((uint64_t)w.x < p.drop_thr) z = p.fill;
+    const float z = hit ? fminf(m * tmax, cam.d_max) : cam.d_max;
+    if (cam.ds > 1) {
+        // downsampled camera: keep the raw depth; downsample_kernel averages and finishes it
+        p.raw[(int64_t)e * p.raw_per_env + cam.raw_off + (int64_t)y * cam.width + x] = z;
     } else {
-        z = fminf(fmaxf(z, cam.d_min), cam.d_max);
-    }
-    const int64_t o_idx = (int64_t)e * p.pix_per_env + col;
-    if (p.out_dtype == RPL_OUT_F32) {
-        static_cast<float *>(p.out)[o_idx] = z;
-    } else if (p.out_dtype == RPL_OUT_F16) {
-        static_cast<__half *>(p.out)[o_idx] = __float2half_rn(z);
-    } else {
-        const float q = rintf(fminf(fmaxf(z / cam.d_max, 0.f), 1.f) * 65535.f);
-        static_cast<uint16_t *>(p.out)[o_idx] = (uint16_t)q;
+        finish_pixel(p, e, c, cam, x, y, z, step, __float_as_uint(CV.w));
     }
 
     if (kCount) {
@@ -797,6 +838,30 @@ __global__ void __launch_bounds__(128, kMinBlocks)
     }
 }
 
+// Output pixels of downsampled cameras: one thread per output pixel of one env (grid-stride over
+// E x pix_per_env); the mean of the f x f raw depths, summed row by row in FP32, then the sensor.
+__global__ void __launch_bounds__(256) downsample_kernel(const __grid_constant__ RenderParams p) {
+    const int64_t total = (int64_t)p.E * p.pix_per_env;
+    const int64_t step = p.step_dev ? *p.step_dev : p.step;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i / p.pix_per_env);
+        const int col = (int)(i - (int64_t)e * p.pix_per_env);
+        int c = 0;
+        while (c + 1 < p.C && col >= p.cams[c + 1].pix_off) ++c;
+        const CamDev &cam = p.cams[c];
+        if (cam.ds <= 1) continue;
+        const int pix = col - cam.pix_off;
+        const int y = pix / cam.out_w, x = pix - y * cam.out_w;
+        const float *src = p.raw + (int64_t)e * p.raw_per_env + cam.raw_off + (int64_t)(y * cam.ds) * cam.width + x * cam.ds;
+        float sum = 0.f;
+        for (int j = 0; j < cam.ds; ++j)
+            for (int k = 0; k < cam.ds; ++k) sum += src[(int64_t)j * cam.width + k];
+        const float z = __fdiv_rn(sum, (float)(cam.ds * cam.ds));
+        const float4 CV = __ldg(p.cam_xf + 5 * ((int64_t)e * p.C + c) + 4);
+        finish_pixel(p, e, c, cam, x, y, z, step, __float_as_uint(CV.w));
+    }
+}
+
 // Graph replays read the step from device memory; this advances it after each replayed render.
 __global__ void advance_step_kernel(int64_t *step) { *step += 1; }
 
@@ -844,6 +909,19 @@ cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
         else
             render_kernel<false, false, 8><<<g, 128, 0, s>>>(p);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_downsample(const RenderParams &p, cudaStream_t s) {
+    const int64_t n = (int64_t)p.E * p.pix_per_env;
+    if (p.raw_per_env == 0 || n == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    int64_t blocks = (n + 255) / 256;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
+                                                   cudaSuccess && sms > 0)
+        blocks = std::min<int64_t>(blocks, (int64_t)sms * 8);
+    (void)cudaGetLastError();
+    downsample_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

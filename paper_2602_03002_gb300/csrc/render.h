@@ -7,10 +7,13 @@
 
 namespace rpl {
 
-// One camera as the kernels see it.  Tiles are 8 x 4 pixels (one warp); tile_off / pix_off are the
-// camera's first tile / pixel inside one env.
+// One camera as the kernels see it.  width x height is the ray-cast (raw) image, tiled by warps of
+// 32 rays; tile_off is the camera's first tile inside one env.  The output image is out_w x out_h
+// = raw / ds; pix_off is its first pixel inside one env's output, raw_off (ds > 1 only) the first
+// pixel of the raw image inside one env's raw buffer.
 struct CamDev {
     int32_t width, height, tiles_x, tile_off;
+    int32_t ds, out_w, out_h, raw_off;
     int32_t pix_off, mount;
     float fx, fy, cx, cy, d_min, d_max;
     float off_pos[3];
@@ -30,6 +33,7 @@ struct PrepParams {
     const float4 *tnodes;      // terrain BVH nodes (binary layout, or wide layout when wide != 0)
     int32_t wide;              // 1: terrain nodes are 80-byte eight-wide quantised nodes (bvh8.h)
     const float *intr;         // [E, C, 4] per-env intrinsics or null
+    const float *mount_dr;     // [E, C, 7] per-env mount perturbation (dp, dq xyzw) or null
     float4 *link_xf;
     float4 *link_box;
     float4 *cam_xf;
@@ -77,6 +81,10 @@ struct RenderParams {
     float sigma_abs, sigma_rel, fill;
     int32_t sensor_on;
     float *ring;                    // [E, span, pix_per_env] or null when span == 1
+    float *raw;                     // [E, raw_per_env] raw depths of downsampled cameras, or null
+    int32_t raw_per_env;
+    const uint8_t *rsm_mode;        // [E] side-mask mode per env, or null (masking off)
+    int32_t rsm_cols[3];            // columns masked on each side per mode
     const int64_t *s_first;         // [E]
     void *out;                      // [E, pix_per_env] of out_dtype
     int32_t *err;                   // error word (bit 0: traversal stack overflow)
@@ -85,6 +93,9 @@ struct RenderParams {
 
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s);
 cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s);
+// Averages the raw images of downsampled cameras and applies the sensor model to them (no-op when
+// p.raw_per_env == 0).  Runs after launch_render of the same parameters.
+cudaError_t launch_downsample(const RenderParams &p, cudaStream_t s);
 cudaError_t launch_set_first(int64_t *s_first, int32_t E, int64_t step, const uint8_t *mask, cudaStream_t s);
 cudaError_t launch_advance_step(int64_t *step, cudaStream_t s);
 // One launch over several requests: reqs_dev[n_req] parameters in device memory, prefix_dev[n_req + 1]

@@ -145,6 +145,14 @@ struct rpl_view {
     bool cams_set = false;
     rpl_sensor_params sensor{};
     DevBuf link_xf, link_box, cam_xf, intr, ring, s_first, mask_stage, pose_stage, out_stage;
+    // downsampled cameras: raw depths [E, raw_per_env]; camera c's raw image starts at raw_off[c]
+    DevBuf raw;
+    int64_t raw_per_env = 0;
+    int64_t raw_off[RPL_MAX_CAMERAS] = {};
+    DevBuf mount_dr;                 // [E, C, 7] per-env mount perturbation (rpl_cameras_randomize)
+    DevBuf rsm_mode;                 // [E] side-mask modes (rpl_side_mask_set)
+    int32_t rsm_cols[3] = {0, 0, 0};
+    bool rsm_on = false;
     int32_t *err_host = nullptr;   // mapped pinned word written by the kernels
     int32_t *err_dev = nullptr;
     bool has_last = false;
@@ -506,12 +514,17 @@ RPL_API rpl_status rpl_cameras_set(rpl_view_t v, const rpl_camera *cams, int32_t
     if (!v || !cams) return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: NULL argument");
     if (n_cams < 1) return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: need at least one camera");
     if (n_cams > RPL_MAX_CAMERAS) return fail(RPL_ERR_CAPACITY, "rpl_cameras_set: more than %d cameras", RPL_MAX_CAMERAS);
-    int64_t off = 0;
+    int64_t off = 0, raw = 0;
+    int64_t raw_off[RPL_MAX_CAMERAS] = {};
     int32_t toff = 0;
     for (int c = 0; c < n_cams; ++c) {
         const rpl_camera &k = cams[c];
         if (k.width <= 0 || k.height <= 0 || k.width > 16384 || k.height > 16384)
             return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: camera %d size %dx%d", c, k.width, k.height);
+        const int32_t ds = k.downsample <= 1 ? 1 : k.downsample;
+        if (k.downsample < 0 || k.downsample > 16 || k.width % ds != 0 || k.height % ds != 0)
+            return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: camera %d downsample %d must be 0..16 and divide %dx%d",
+                        c, k.downsample, k.width, k.height);
         if (!(k.fx != 0.f) || !(k.fy != 0.f) || !std::isfinite(k.fx) || !std::isfinite(k.fy))
             return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: camera %d has fx or fy 0", c);
         if (k.mount_link < 0 || k.mount_link >= v->L)
@@ -521,10 +534,15 @@ RPL_API rpl_status rpl_cameras_set(rpl_view_t v, const rpl_camera *cams, int32_t
             return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: camera %d needs 0 < d_max, d_min <= d_max", c);
         v->cam_off[c] = off;
         v->tile_off[c] = toff;
-        off += (int64_t)k.width * k.height;
+        off += (int64_t)(k.width / ds) * (k.height / ds);
         toff += ((k.width + 7) / 8) * ((k.height + 3) / 4);
+        if (ds > 1) {
+            raw_off[c] = raw;
+            raw += (int64_t)k.width * k.height;
+        }
     }
-    if (off >= (int64_t)1 << 31) return fail(RPL_ERR_CAPACITY, "rpl_cameras_set: too many pixels per env");
+    if (off >= (int64_t)1 << 31 || raw >= (int64_t)1 << 31)
+        return fail(RPL_ERR_CAPACITY, "rpl_cameras_set: too many pixels per env");
     DeviceGuard g(v->scene->device);
     for (int c = 0; c < n_cams; ++c) v->cams[c] = cams[c];
     v->cam_off[n_cams] = off;
@@ -535,6 +553,15 @@ RPL_API rpl_status rpl_cameras_set(rpl_view_t v, const rpl_camera *cams, int32_t
     v->gen++;
     cudaError_t e = v->cam_xf.alloc((size_t)v->E * n_cams * 5 * sizeof(float4));
     if (e != cudaSuccess) return cuda_fail(e, "rpl_cameras_set: allocating camera transforms");
+    v->raw_per_env = raw;
+    for (int c = 0; c < n_cams; ++c) v->raw_off[c] = raw_off[c];
+    if (raw > 0) {
+        e = v->raw.alloc((size_t)v->E * raw * sizeof(float));
+        if (e != cudaSuccess) return cuda_fail(e, "rpl_cameras_set: allocating the raw-depth buffer");
+    } else {
+        v->raw.release();
+    }
+    v->mount_dr.release();
     if (per_env_intr) {
         const size_t bytes = (size_t)v->E * n_cams * 4 * sizeof(float);
         std::vector<char> h;
@@ -554,6 +581,58 @@ RPL_API rpl_status rpl_cameras_set(rpl_view_t v, const rpl_camera *cams, int32_t
     v->has_last = false;
     v->need_first = true;
     return alloc_ring(v);
+}
+
+RPL_API rpl_status rpl_cameras_randomize(rpl_view_t v, const float *mount_delta) {
+    if (!v) return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_randomize: view is NULL");
+    if (!v->cams_set) return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_randomize: cameras not set");
+    DeviceGuard g(v->scene->device);
+    v->gen++;   // a captured graph holds the buffer's address
+    if (!mount_delta) {
+        v->mount_dr.release();
+        return RPL_OK;
+    }
+    const size_t n = (size_t)v->E * v->C;
+    std::vector<char> h;
+    rpl_status st = to_host(mount_delta, n * 7 * sizeof(float), v->scene->device, h);
+    if (st != RPL_OK) return st;
+    float *d = reinterpret_cast<float *>(h.data());
+    for (size_t i = 0; i < n; ++i) {
+        float *q = d + 7 * i + 3;
+        const double nq = std::sqrt((double)q[0] * q[0] + (double)q[1] * q[1] + (double)q[2] * q[2] + (double)q[3] * q[3]);
+        if (!(nq > 0) || !std::isfinite(nq) || !std::isfinite(d[7 * i]) || !std::isfinite(d[7 * i + 1]) ||
+            !std::isfinite(d[7 * i + 2]))
+            return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_randomize: entry %zu has a zero or non-finite value", i);
+        for (int k = 0; k < 4; ++k) q[k] = (float)(q[k] / nq);
+    }
+    if (v->has_done) cudaEventSynchronize(v->done);   // an enqueued render may still read the old values
+    cudaError_t e = v->mount_dr.bytes >= std::max<size_t>(n * 7 * sizeof(float), 16) ? cudaSuccess
+                                                                                       : v->mount_dr.alloc(n * 7 * sizeof(float));
+    if (e == cudaSuccess && n) e = cudaMemcpy(v->mount_dr.p, h.data(), n * 7 * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_cameras_randomize: uploading the mount perturbations");
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_side_mask_set(rpl_view_t v, const int32_t cols[3], const uint8_t *env_mode) {
+    if (!v) return fail(RPL_ERR_INVALID_ARG, "rpl_side_mask_set: view is NULL");
+    DeviceGuard g(v->scene->device);
+    v->gen++;
+    if (!env_mode) {
+        v->rsm_on = false;
+        return RPL_OK;
+    }
+    if (!cols || cols[0] < 0 || cols[1] < 0 || cols[2] < 0)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_side_mask_set: cols must be three values >= 0");
+    std::vector<char> h;
+    rpl_status st = to_host(env_mode, (size_t)v->E, v->scene->device, h);
+    if (st != RPL_OK) return st;
+    if (v->has_done) cudaEventSynchronize(v->done);   // an enqueued render may still read the old modes
+    cudaError_t e = v->rsm_mode.bytes >= std::max<size_t>((size_t)v->E, 16) ? cudaSuccess : v->rsm_mode.alloc((size_t)v->E);
+    if (e == cudaSuccess && v->E) e = cudaMemcpy(v->rsm_mode.p, h.data(), (size_t)v->E, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_side_mask_set: uploading the modes");
+    for (int k = 0; k < 3; ++k) v->rsm_cols[k] = cols[k];
+    v->rsm_on = true;
+    return RPL_OK;
 }
 
 RPL_API rpl_status rpl_sensor_set(rpl_view_t v, const rpl_sensor_params *prm) {
@@ -598,6 +677,10 @@ static int32_t fill_cams(const rpl_view *v, CamDev *out) {
         d.tiles_x = (k.width + tw - 1) / tw;
         d.tile_off = toff;
         toff += d.tiles_x * ((k.height + th - 1) / th);
+        d.ds = k.downsample <= 1 ? 1 : k.downsample;
+        d.out_w = k.width / d.ds;
+        d.out_h = k.height / d.ds;
+        d.raw_off = (int32_t)v->raw_off[c];
         d.pix_off = (int32_t)v->cam_off[c];
         d.mount = k.mount_link;
         d.fx = k.fx;
@@ -614,14 +697,14 @@ static int32_t fill_cams(const rpl_view *v, CamDev *out) {
 
 static size_t out_elem_bytes(const rpl_view *v) { return v->sensor.out_dtype == RPL_OUT_F32 ? 4 : 2; }
 
-// Prep and render parameters of one render of view v (device buffers); launches the sensor-state
-// reset on `st` first when the view needs one.  step_dev (graph capture only) makes both kernels
-// read the step from device memory instead of `step`.
 // Marks the end of the work just enqueued for `v` on `st`.
 static void mark_done(rpl_view *v, cudaStream_t st) {
     if (cudaEventRecord(v->done, st) == cudaSuccess) v->has_done = true;
 }
 
+// Prep and render parameters of one render of view v (device buffers); launches the sensor-state
+// reset on `st` first when the view needs one.  step_dev (graph capture only) makes both kernels
+// read the step from device memory instead of `step`.
 static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step, int64_t env_offset, void *out_dev,
                                cudaStream_t st, unsigned long long *counters_dev, const int64_t *step_dev,
                                PrepParams &pp, RenderParams &rp) {
@@ -638,6 +721,7 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
     pp.tnodes = s->t_nodes.as<const float4>();
     pp.wide = s->opts.bvh_kind == RPL_BVH8Q8 ? 1 : 0;
     pp.intr = v->intr.p ? v->intr.as<const float>() : nullptr;
+    pp.mount_dr = v->mount_dr.p ? v->mount_dr.as<const float>() : nullptr;
     for (int l = 0; l < RPL_MAX_LINKS; ++l) pp.lroot[l] = l < v->L ? s->l_root[l] : -1;
     pp.link_xf = v->link_xf.as<float4>();
     pp.link_box = v->link_box.as<float4>();
@@ -691,6 +775,10 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
     rp.fill = sp.fill;
     rp.sensor_on = (sp.sigma_abs != 0.f || sp.sigma_rel != 0.f || sp.p_drop != 0.f || sp.max_latency != 0) ? 1 : 0;
     rp.ring = rp.span > 1 ? v->ring.as<float>() : nullptr;
+    rp.raw = v->raw_per_env > 0 ? v->raw.as<float>() : nullptr;
+    rp.raw_per_env = (int32_t)v->raw_per_env;
+    rp.rsm_mode = v->rsm_on ? v->rsm_mode.as<const uint8_t>() : nullptr;
+    for (int k = 0; k < 3; ++k) rp.rsm_cols[k] = v->rsm_cols[k];
     rp.s_first = v->s_first.as<const int64_t>();
     rp.out = out_dev;
     rp.err = v->err_dev;
@@ -713,6 +801,8 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
     if (timed) cudaEventRecord(v->ev[2 * slot], st);
     e = launch_render(rp, count, st);
     if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the render kernel");
+    e = launch_downsample(rp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the downsample kernel");
     if (timed) {
         cudaEventRecord(v->ev[2 * slot + 1], st);
         v->n_timed++;

@@ -169,6 +169,8 @@ void launch_batch(rpl_server *sv, Slot &s) {
     if (e == cudaSuccess)
         e = launch_render_multi(s.d_params, s.d_prefix, n, total, sv->wide, sv->opts.min_blocks,
                                 sv->opts.persistent != 0, st);
+    for (int i = 0; i < n && e == cudaSuccess; ++i)   // downsampled cameras of a request: average + sensor
+        if (s.reqs[i]->status == RPL_OK && s.h_params[i].raw_per_env > 0) e = launch_downsample(s.h_params[i], st);
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         Request *r = s.reqs[i];
         if (r->out_host && r->status == RPL_OK)

@@ -42,7 +42,8 @@ class rpl_camera(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fx", ctypes.c_float),
                 ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
                 ("mount_link", ctypes.c_int32), ("offset_pos", ctypes.c_float * 3),
-                ("offset_quat_xyzw", ctypes.c_float * 4), ("d_min", ctypes.c_float), ("d_max", ctypes.c_float)]
+                ("offset_quat_xyzw", ctypes.c_float * 4), ("d_min", ctypes.c_float), ("d_max", ctypes.c_float),
+                ("downsample", ctypes.c_int32)]
 
 
 class rpl_sensor_params(ctypes.Structure):
@@ -84,7 +85,7 @@ class rpl_counters(ctypes.Structure):
 
 
 EXPORTS = ["rpl_bvh_build_host", "rpl_bvh8_build_host", "rpl_scene_create", "rpl_link_mesh_add", "rpl_scene_info_get", "rpl_scene_destroy", "rpl_view_create",
-           "rpl_cameras_set", "rpl_sensor_set", "rpl_view_layout", "rpl_render", "rpl_view_reset", "rpl_sync",
+           "rpl_cameras_set", "rpl_cameras_randomize", "rpl_side_mask_set", "rpl_sensor_set", "rpl_view_layout", "rpl_render", "rpl_view_reset", "rpl_sync",
            "rpl_render_counters", "rpl_view_timing", "rpl_view_kernel_ms", "rpl_view_destroy", "rpl_last_error",
            "rpl_version", "rpl_render_static_scratch", "rpl_view_tuning_set", "rpl_view_tuning_get",
            "rpl_view_autotune", "rpl_render_graph", "rpl_server_create", "rpl_server_submit", "rpl_server_wait",
@@ -111,6 +112,8 @@ def lib() -> ctypes.CDLL:
         "rpl_scene_destroy": ([P], None),
         "rpl_view_create": ([P, I32, I32, P], I32),
         "rpl_cameras_set": ([P, P, I32, P], I32),
+        "rpl_cameras_randomize": ([P, P], I32),
+        "rpl_side_mask_set": ([P, P, P], I32),
         "rpl_sensor_set": ([P, P], I32),
         "rpl_view_layout": ([P, P, P], I32),
         "rpl_render": ([P, P, I64, I64, P, P], I32),
@@ -234,10 +237,10 @@ def rpl_view_create(scene: int, n_envs: int, n_links: int) -> int:
 
 
 def _camera_struct(c) -> rpl_camera:
-    g = (lambda k: c[k]) if isinstance(c, dict) else (lambda k: getattr(c, k))
+    g = (lambda k, d=None: c.get(k, d)) if isinstance(c, dict) else (lambda k, d=None: getattr(c, k, d))
     return rpl_camera(int(g("width")), int(g("height")), g("fx"), g("fy"), g("cx"), g("cy"), int(g("mount_link")),
                       (ctypes.c_float * 3)(*g("offset_pos")), (ctypes.c_float * 4)(*g("offset_quat")),
-                      g("d_min"), g("d_max"))
+                      g("d_min"), g("d_max"), int(g("downsample", 1)))
 
 
 def rpl_cameras_set(view: int, cams: Sequence, per_env_intrinsics=None):
@@ -246,6 +249,21 @@ def rpl_cameras_set(view: int, cams: Sequence, per_env_intrinsics=None):
     if isinstance(intr, np.ndarray):
         intr = np.ascontiguousarray(intr, np.float32)
     _check(lib().rpl_cameras_set(view, arr, len(cams), _ptr(intr)))
+
+
+def rpl_cameras_randomize(view: int, mount_delta=None):
+    """mount_delta: None or [E, C, 7] (dp xyz, dq xyzw), numpy or torch (host or device)."""
+    if isinstance(mount_delta, np.ndarray):
+        mount_delta = np.ascontiguousarray(mount_delta, np.float32)
+    _check(lib().rpl_cameras_randomize(view, _ptr(mount_delta)))
+
+
+def rpl_side_mask_set(view: int, cols=(0, 0, 0), env_mode=None):
+    """env_mode: None (off) or [E] uint8 modes 0/1/2; cols: columns masked per side for each mode."""
+    if isinstance(env_mode, np.ndarray):
+        env_mode = np.ascontiguousarray(env_mode, np.uint8)
+    c = (ctypes.c_int32 * 3)(*[int(v) for v in cols])
+    _check(lib().rpl_side_mask_set(view, c, _ptr(env_mode)))
 
 
 def _sensor_struct(s) -> rpl_sensor_params:
@@ -397,12 +415,24 @@ class View:
     def from_workload(cls, scene: Scene, w, n_envs: Optional[int] = None) -> "View":
         v = cls(scene, w.n_envs if n_envs is None else n_envs, w.n_links)
         v.set_cameras(w.cameras, w.per_env_intrinsics)
+        if getattr(w, "mount_delta", None) is not None:
+            v.randomize_cameras(w.mount_delta)
+        if getattr(w, "rsm_modes", None) is not None:
+            v.set_side_mask(w.rsm_cols, w.rsm_modes)
         v.set_sensor(w.sensor)
         return v
 
     def set_cameras(self, cams, per_env_intrinsics=None):
         rpl_cameras_set(self.h, cams, per_env_intrinsics)
         self.cams = list(cams)
+
+    def randomize_cameras(self, mount_delta=None):
+        """Per-env camera mount perturbation [E, C, 7] (dp xyz, dq xyzw), or None to clear."""
+        rpl_cameras_randomize(self.h, mount_delta)
+
+    def set_side_mask(self, cols=(0, 0, 0), env_mode=None):
+        """Random Side Masking: env_mode [E] (0 none, 1 small, 2 large), cols per mode; None = off."""
+        rpl_side_mask_set(self.h, cols, env_mode)
 
     def set_sensor(self, sensor):
         rpl_sensor_set(self.h, sensor)

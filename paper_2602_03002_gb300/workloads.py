@@ -86,6 +86,9 @@ class Workload:
     sensor: Sensor
     step0: int = 0                       # step number of poses[0]
     per_env_intrinsics: Optional[np.ndarray] = None  # [E,C,4] float32 (fx,fy,cx,cy) or None
+    mount_delta: Optional[np.ndarray] = None         # [E,C,7] float32 (dp xyz, dq xyzw) or None
+    rsm_modes: Optional[np.ndarray] = None           # [E] uint8 side-mask modes or None
+    rsm_cols: Tuple[int, int, int] = (0, 0, 0)       # columns masked per side for modes 0, 1, 2
 
     @property
     def n_steps(self) -> int:
@@ -101,17 +104,23 @@ class Workload:
 
     @property
     def pixels_per_env(self) -> int:
+        """Output pixels per env (downsampled images count at their output size)."""
+        return int(sum(c.out_width * c.out_height for c in self.cameras))
+
+    @property
+    def raw_pixels_per_env(self) -> int:
+        """Ray-cast pixels per env (downsampled cameras count at their raw size)."""
         return int(sum(c.width * c.height for c in self.cameras))
 
     @property
     def rays_per_step(self) -> int:
-        return self.n_envs * self.pixels_per_env
+        return self.n_envs * self.raw_pixels_per_env
 
     def cam_offsets(self) -> np.ndarray:
         """Start of each camera's pixels inside one env's packed output row."""
         off = [0]
         for c in self.cameras:
-            off.append(off[-1] + c.width * c.height)
+            off.append(off[-1] + c.out_width * c.out_height)
         return np.asarray(off, dtype=np.int64)
 
     def link_arrays(self):
@@ -496,5 +505,100 @@ def config_uneven(n_steps: int = 4, n_envs: int = 4096, tiles: int = 20, cell: f
                         sensor=Sensor(), seed=seed)
 
 
+# --------------------------------------------------------------------------------------------------
+# The paper's perception settings (Sec. 4.1) and randomisation (Appendix A.2; Sec. 3.2.4)
+# --------------------------------------------------------------------------------------------------
+def _quat_axis(axis: int, ang: np.ndarray) -> np.ndarray:
+    """Quaternions (x, y, z, w) of rotations by `ang` radians about coordinate axis 0, 1 or 2."""
+    q = np.zeros(ang.shape + (4,))
+    q[..., axis] = np.sin(ang / 2.0)
+    q[..., 3] = np.cos(ang / 2.0)
+    return q
+
+
+def _quat_mul(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Hamilton product a * b of (x, y, z, w) quaternions (rotation b first, then a)."""
+    ax, ay, az, aw = np.moveaxis(a, -1, 0)
+    bx, by, bz, bw = np.moveaxis(b, -1, 0)
+    return np.stack([aw * bx + ax * bw + ay * bz - az * by,
+                     aw * by - ax * bz + ay * bw + az * bx,
+                     aw * bz + ax * by - ay * bx + az * bw,
+                     aw * bw - ax * bx - ay * by - az * bz], axis=-1)
+
+
+def camera_randomization(n_envs: int, cams: Sequence[Camera], seed: int = 0, dpos: float = 0.025,
+                         euler_deg: Tuple[float, float, float] = (2.5, 3.0, 2.5), dfov_deg: float = 2.0):
+    """Per-env camera draws of the perception randomisation (Appendix A.2): mount translation
+    U(+-dpos) per axis; rotation by Euler angles (roll, pitch, yaw) U(+-2.5, +-3.0, +-2.5) deg about
+    the camera's optical axis z, right axis x and down axis y, composed as R_z(roll) R_x(pitch)
+    R_y(yaw); FOV change dFOV U(+-2) deg added to the horizontal FOV, both focal lengths scaled by
+    the same factor (square pixels kept).  Returns (mount_delta [E,C,7], per_env_intrinsics [E,C,4])."""
+    rng = np.random.default_rng(seed + 17)
+    C = len(cams)
+    dp = rng.uniform(-dpos, dpos, size=(n_envs, C, 3))
+    ang = np.radians(np.stack([rng.uniform(-a, a, size=(n_envs, C)) for a in euler_deg], axis=-1))
+    dq = _quat_mul(_quat_mul(_quat_axis(2, ang[..., 0]), _quat_axis(0, ang[..., 1])), _quat_axis(1, ang[..., 2]))
+    dfov = np.radians(rng.uniform(-dfov_deg, dfov_deg, size=(n_envs, C)))
+    intr = np.zeros((n_envs, C, 4), np.float32)
+    for c, cam in enumerate(cams):
+        hfov = 2.0 * np.arctan(cam.width / (2.0 * cam.fx))
+        scale = np.tan(hfov / 2.0) / np.tan((hfov + dfov[:, c]) / 2.0)
+        intr[:, c, 0] = cam.fx * scale
+        intr[:, c, 1] = cam.fy * scale
+        intr[:, c, 2] = cam.cx
+        intr[:, c, 3] = cam.cy
+    return np.concatenate([dp, dq], axis=-1).astype(np.float32), intr
+
+
+# Side-mask mode probabilities (none, small, large) per terrain kind: larger masks on continuous
+# terrain (stairs, slopes), smaller ones on stepping stones (Sec. 3.2.4 gives the ordering only).
+RSM_PROBS = {"continuous": (0.4, 0.2, 0.4), "stones": (0.5, 0.4, 0.1)}
+
+
+def side_mask_modes(n_envs: int, tiles: int = 20, seed: int = 0) -> np.ndarray:
+    """Mode per env (0 none, 1 small, 2 large) drawn from RSM_PROBS by the kind of the env's tile
+    (env e stands on tile e mod tiles^2, as scale_envs places it)."""
+    rng = np.random.default_rng(seed + 23)
+    tile = np.arange(n_envs) % (tiles * tiles)
+    kind = (tile // tiles + tile % tiles) % 5
+    u = rng.uniform(size=n_envs)
+    modes = np.zeros(n_envs, np.uint8)
+    for stones, probs in ((False, RSM_PROBS["continuous"]), (True, RSM_PROBS["stones"])):
+        m = (kind == 4) == stones
+        modes[m] = np.where(u[m] < probs[0], 0, np.where(u[m] < probs[0] + probs[1], 1, 2))
+    return modes
+
+
+def perception_sensor() -> Sensor:
+    """The paper's depth randomisation preset: sigma = 0.1 depth, 5 % dropout; latency 0-3 steps."""
+    return Sensor(sigma_abs=0.0, sigma_rel=0.1, p_drop=0.05, fill=0.0, max_latency=3, seed=(0x52504C31, 1))
+
+
+def perception_cameras(torso: int, n_cams: int = 2, raw=(240, 135), downsample: int = 5):
+    """Torso cameras with the paper's perception settings (Sec. 4.1): FOV 101 x 69 deg, raw 240x135
+    rendered and downsampled to 48x27; front/back, then left/right for four cameras."""
+    cams = _torso_cameras(torso, [raw] * n_cams, hfov=101.0, vfov=69.0)
+    for c in cams:
+        c.downsample = downsample
+    return cams
+
+
+def config_perception(n_steps: int = 4, n_envs: int = 4096, tiles: int = 20, cell: float = 0.05, n_cams: int = 2,
+                      seed: int = 0, rsm_cols: Tuple[int, int, int] = (0, 6, 12)) -> Workload:
+    """The scale terrain and robot with the paper's cameras: 240x135 raw downsampled to 48x27 (101 x 69
+    deg), per-env camera pose and FOV randomisation, side masking by terrain kind, sensor preset."""
+    tv, tt = _scale_terrain(tiles, cell)
+    links, torso = _robot(30)
+    lv, lt = _link_meshes(links, "ellipsoid")
+    poses, _ = scale_envs(n_envs, n_steps, tiles, seed=seed)
+    cams = perception_cameras(torso, n_cams)
+    md, intr = camera_randomization(n_envs, cams, seed)
+    return Workload("perception: %d envs x %d cams 240x135 -> 48x27, %d-tri terrain, camera DR, side masking"
+                    % (n_envs, n_cams, len(tt)), tv, tt, lv, lt, cams, poses, perception_sensor(),
+                    per_env_intrinsics=intr, mount_delta=md, rsm_modes=side_mask_modes(n_envs, tiles, seed),
+                    rsm_cols=rsm_cols)
+
+
 def make_workload(name: str, **kw) -> Workload:
-    return {"small": config_small, "scale": config_scale, "uneven": config_uneven}[name](**kw)
+    return {"small": config_small, "scale": config_scale, "uneven": config_uneven,
+            "perception": config_perception}[name](**kw)

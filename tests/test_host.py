@@ -212,3 +212,31 @@ def test_cameras_start_outside_every_link(cfg):
                     n = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
                     side = np.einsum("ij,ij->i", n, ol - tri[:, 0])
                     assert side.max() > 0, (s, e, l)     # in front of some face of the convex mesh
+
+
+def test_perception_generators():
+    """The paper's camera settings and randomisation draws (Sec. 4.1, Appendix A.2, Sec. 3.2.4)."""
+    cams = W.perception_cameras(3, 4)
+    assert [(c.width, c.height, c.out_width, c.out_height) for c in cams] == [(240, 135, 48, 27)] * 4
+    hfov = np.degrees(2 * np.arctan(240 / (2 * cams[0].fx)))
+    vfov = np.degrees(2 * np.arctan(135 / (2 * cams[0].fy)))
+    assert abs(hfov - 101.0) < 1e-3 and abs(vfov - 69.0) < 1e-3
+    E = 2000
+    md, intr = W.camera_randomization(E, cams, seed=5)
+    assert md.shape == (E, 4, 7) and intr.shape == (E, 4, 4)
+    assert np.abs(md[..., :3]).max() <= 0.025 and np.abs(md[..., :3]).max() > 0.02
+    q = md[..., 3:].reshape(-1, 4).astype(np.float64)
+    np.testing.assert_allclose(np.linalg.norm(q, axis=1), 1.0, atol=1e-6)
+    # Euler angles back from the quaternions (scipy, intrinsic z-x-y = the composition order)
+    ang = Rotation.from_quat(q).as_euler("ZXY", degrees=True)
+    assert np.all(np.abs(ang) <= np.array([2.5, 3.0, 2.5]) + 1e-4)
+    assert np.all(np.abs(ang).max(axis=0) > np.array([2.4, 2.9, 2.4]))
+    new_hfov = np.degrees(2 * np.arctan(240 / (2 * intr[..., 0].astype(np.float64))))
+    assert np.all(np.abs(new_hfov - hfov) <= 2.0 + 1e-3) and np.abs(new_hfov - hfov).max() > 1.9
+    np.testing.assert_allclose(intr[..., 1] / intr[..., 0], cams[0].fy / cams[0].fx, rtol=1e-6)
+    modes = W.side_mask_modes(40000, tiles=20, seed=1)
+    tile = np.arange(40000) % 400
+    stones = (tile // 20 + tile % 20) % 5 == 4
+    for sel, probs in ((~stones, W.RSM_PROBS["continuous"]), (stones, W.RSM_PROBS["stones"])):
+        freq = np.bincount(modes[sel], minlength=3) / sel.sum()
+        assert np.all(np.abs(freq - np.asarray(probs)) < 5 * np.sqrt(0.25 / sel.sum()))
