@@ -6,7 +6,11 @@ Variants (``--variant``):
              sensor on (0.01 m noise, 2 % dropout, latency 0-3), binary BVH, FP32 depth (default);
   precision  the same with the eight-wide BVH of 8-bit quantised boxes and FP16 depth;
   batching   4096 envs x 4 uneven cameras (80x60, 80x60, 48x36, 48x36) in one launch, replayed as a
-             CUDA graph of the whole path.
+             CUDA graph of the whole path;
+  perception the paper's perception settings: 4096 envs x 2 cameras ray cast at 240x135 and averaged
+             to 48x27 (101 x 69 deg FOV), per-env camera pose and FOV randomisation, side masking by
+             terrain kind, sensor preset sigma = 0.1 depth, 5 % dropout, latency 0-3;
+  serving    Poisson request streams from 4 trainers through the continuous-batching server.
 One step = the whole path over all envs with the next resident pose set: rpl_render (prep + render
 kernels), or one graph replay for ``batching``.  The launch shape is chosen by the library's
 autotuner before timing.  Rank 0 prints one JSON line.  ``--impl reference`` times the FP64 CPU
@@ -44,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variant", default="plain", choices=["plain", "precision", "batching", "serving"])
+    ap.add_argument("--variant", default="plain", choices=["plain", "precision", "batching", "perception", "serving"])
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--tiles", type=int, default=20)
     ap.add_argument("--pose-sets", type=int, default=8)
@@ -65,6 +69,8 @@ def workload(args, rank):
     from paper_2602_03002_gb300 import workloads as W
     if args.variant == "batching":
         return W.config_uneven(n_steps=args.pose_sets, n_envs=args.envs, tiles=args.tiles, seed=rank)
+    if args.variant == "perception":
+        return W.config_perception(n_steps=args.pose_sets, n_envs=args.envs, tiles=args.tiles, seed=rank)
     w = W.config_scale(n_steps=args.pose_sets, n_envs=args.envs, tiles=args.tiles, seed=rank)
     if args.variant == "precision":
         w.sensor.out_dtype = 1
@@ -72,12 +78,15 @@ def workload(args, rank):
 
 
 def workload_name(w, variant):
-    cams = " + ".join("%dx%d" % (c.width, c.height) for c in w.cameras)
+    cams = " + ".join("%dx%d" % (c.width, c.height) + ("->%dx%d" % (c.out_width, c.out_height) if c.downsample > 1 else "")
+                      for c in w.cameras)
     s = w.sensor
-    sensor = ("sensor sigma %.2f m, %.0f%% dropout, latency 0-%d steps" % (s.sigma_abs, 100 * s.p_drop, s.max_latency)
-              if s.enabled else "no sensor model")
+    sensor = ("sensor sigma %.2f m + %.2f depth, %.0f%% dropout, latency 0-%d steps"
+              % (s.sigma_abs, s.sigma_rel, 100 * s.p_drop, s.max_latency) if s.enabled else "no sensor model")
     form = {"plain": "binary BVH, FP32 depth", "precision": "8-wide BVH with 8-bit quantised boxes, FP16 depth",
-            "batching": "binary BVH, FP32 depth, one CUDA-graph replay per step"}[variant]
+            "batching": "binary BVH, FP32 depth, one CUDA-graph replay per step",
+            "perception": "binary BVH, FP32 depth, raw images block-averaged before the sensor, per-env camera "
+                          "pose/FOV randomisation, side masking (cols %s by mode)" % (tuple(w.rsm_cols),)}[variant]
     return ("%s: %d envs x cams (%s px); terrain %d tris (tiles of 8x8 m at 0.05 m: stairs 0.22/0.25/0.30 m run, "
             "20 deg slopes, stepping stones); %d links x %d-tri meshes; %s; %s"
             % (variant, w.n_envs, cams, len(w.terrain_tris), w.n_links, len(w.link_tris[0]), sensor, form))
@@ -157,9 +166,10 @@ class Clocks:
 
 
 def sample_rays(w, n, rng):
+    """n output pixels (env, camera, x, y) drawn uniformly."""
     c = rng.integers(0, len(w.cameras), n)
-    wd = np.array([cam.width for cam in w.cameras])[c]
-    ht = np.array([cam.height for cam in w.cameras])[c]
+    wd = np.array([cam.out_width for cam in w.cameras])[c]
+    ht = np.array([cam.out_height for cam in w.cameras])[c]
     x = (rng.random(n) * wd).astype(np.int64)
     y = (rng.random(n) * ht).astype(np.int64)
     return np.stack([rng.integers(0, w.n_envs, n), c, x, y], 1).astype(np.int64)
@@ -172,21 +182,25 @@ def cpu_baseline(w, seconds, gpu_step0=None):
     cores = os.cpu_count() or 1
     sc = oracle.OracleScene.from_workload(w)
     rng = np.random.default_rng(1234)
+    extra = dict(per_env_intrinsics=w.per_env_intrinsics, mount_dr=w.mount_delta, rsm_mode=w.rsm_modes,
+                 rsm_cols=w.rsm_cols, flags=False, threads=cores)
     t = time.perf_counter()
-    sc.render(w.cameras, w.poses, 0, sample_rays(w, cores, rng), w.sensor, flags=False, threads=cores)
+    sc.render(w.cameras, w.poses, 0, sample_rays(w, cores, rng), w.sensor, **extra)
     probe = time.perf_counter() - t
     n = max(cores, int(cores * seconds / max(probe, 1e-3)))
     rays = sample_rays(w, n, rng)
     t = time.perf_counter()
-    ref = sc.render(w.cameras, w.poses, 0, rays, w.sensor, flags=False, threads=cores)
+    ref = sc.render(w.cameras, w.poses, 0, rays, w.sensor, **extra)
     dt = time.perf_counter() - t
     sc.close()
-    out = {"value": n / dt / 1e9, "unit": "Grays/s", "cores": cores, "kind": "oracle",
-           "sample": "%d rays drawn uniformly over (env, camera, pixel) of step 0, FP64 brute force over all "
-                     "triangles, %.1f s" % (n, dt)}
+    per_px = np.array([max(1, c.downsample) ** 2 for c in w.cameras])[rays[:, 1]]
+    n_rays = int(per_px.sum())                       # a downsampled pixel costs f^2 ray casts
+    out = {"value": n_rays / dt / 1e9, "unit": "Grays/s", "cores": cores, "kind": "oracle",
+           "sample": "%d output pixels (%d ray casts) drawn uniformly over (env, camera, pixel) of step 0, FP64 "
+                     "brute force over all triangles, %.1f s" % (n, n_rays, dt)}
     if gpu_step0 is not None:
         offs = w.cam_offsets()
-        cw = np.array([c.width for c in w.cameras])
+        cw = np.array([c.out_width for c in w.cameras])
         got = gpu_step0[rays[:, 0], offs[rays[:, 1]] + rays[:, 3] * cw[rays[:, 1]] + rays[:, 2]]
         if w.sensor.out_dtype == 2:
             got = got * (w.cameras[0].d_max / 65535.0)
@@ -197,7 +211,7 @@ def cpu_baseline(w, seconds, gpu_step0=None):
                                   "p99_abs_m": float(np.quantile(err, 0.99)), "mean_abs_m": float(err.mean()),
                                   "mismatch_frac": float(np.mean(err > allow)),
                                   "allowance_m": "1e-4" + (" + half an FP16 ulp" if w.sensor.out_dtype == 1 else "")}
-    return n, dt, cores, out
+    return n_rays, dt, cores, out
 
 
 def run_reference(args):
@@ -213,7 +227,7 @@ def run_reference(args):
             n_tot += n
             dt_tot += dt
     rate = n_tot / dt_tot
-    sample = "%d rays per step drawn uniformly over (env, camera, pixel), brute force over all %d triangles" % (
+    sample = "%d ray casts per step for output pixels drawn uniformly over (env, camera, pixel), brute force over all %d triangles" % (
         n_tot // max(1, args.steps), len(w.terrain_tris) + sum(len(t) for t in w.link_tris))
     line = {"impl": "reference", "metric": METRIC, "value": rate / 1e9, "unit": "Grays/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt_tot / max(1, args.steps),
@@ -264,9 +278,11 @@ def run_ours(args):
     b_nodes = cnt["terrain_nodes"] * node_bytes + cnt["link_nodes"] * 64
     b_tris = (cnt["terrain_tris"] + cnt["link_tris"]) * TRI_BYTES
     b_boxes = cnt["link_boxes"] * BOX_BYTES
-    # compulsory per-ray traffic: output store, ring write and (k > 0) ring read
+    # compulsory traffic of the render kernel: per output ray the store, ring write and (k > 0) ring
+    # read; per ray of a downsampled camera the raw-depth store (the downsample kernel does the rest)
     out_b = out.element_size()
-    b_io = rays * (out_b + (8 if w.sensor.max_latency > 0 else 0))
+    raw_rays = w.n_envs * sum(c.width * c.height for c in w.cameras if c.downsample > 1)
+    b_io = (rays - raw_rays) * (out_b + (8 if w.sensor.max_latency > 0 else 0)) + raw_rays * 4
     alg_bytes = b_nodes + b_tris + b_boxes + b_io
 
     tuning, tune_ms = rpl.rpl_view_tuning_get(view.h), None
@@ -365,7 +381,7 @@ def run_ours(args):
                          % (info["terrain_bytes"] / 1e9)},
         "frames_per_s": frames,
         "env_steps_per_s": world * w.n_envs / (ms_step / 1e3),
-        "gpu_launches": (3 if graph else 2) * args.steps,
+        "gpu_launches": ((3 if graph else 2) + (1 if raw_rays else 0)) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic_per_launch(rays, args.variant, tuning),
                      "kernel": "render_kernel", "kernel_ms": 1e3 * k_avg_s,

@@ -801,12 +801,12 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
     if (timed) cudaEventRecord(v->ev[2 * slot], st);
     e = launch_render(rp, count, st);
     if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the render kernel");
-    e = launch_downsample(rp, st);
-    if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the downsample kernel");
     if (timed) {
         cudaEventRecord(v->ev[2 * slot + 1], st);
         v->n_timed++;
     }
+    e = launch_downsample(rp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the downsample kernel");
     if (!step_dev) mark_done(v, st);   // a captured render is marked by rpl_render_graph's launch
     return RPL_OK;
 }
