@@ -248,7 +248,7 @@ RPL_API rpl_status rpl_render(rpl_view_t view, const float *link_poses, int64_t 
  * pixels of one camera); persistent: launch only as many blocks as fit on the GPU at once and let
  * warps stride over the tiles; terrain_first: query the terrain before the links (Alg. 1 queries
  * the bodies first; the depth is the same either way); min_blocks: 8 (up to 64 registers per
- * thread) or 12 (up to 40) resident blocks of 128 threads per SM.  The shape never changes the
+ * thread), 10 (up to 48) or 12 (up to 40) resident blocks of 128 threads per SM.  The shape never changes the
  * result, only the speed.  Default: 8x4, not persistent, links first, 8. */
 typedef struct {
     int32_t tile_w, tile_h;
@@ -261,8 +261,8 @@ RPL_API rpl_status rpl_view_tuning_set(rpl_view_t view, const rpl_tuning *tuning
 RPL_API rpl_status rpl_view_tuning_get(rpl_view_t view, rpl_tuning *tuning);
 
 /* Autotuner: renders `step` (same step rules as rpl_render; device buffers only) `reps` times
- * with each of the 24 launch shapes (tile 8x4 / 4x8 / 16x2, persistent or not, links or terrain
- * first, 8 or 12 blocks per SM), times them with CUDA events on `stream`, keeps the fastest on the
+ * with each of the 36 launch shapes (tile 8x4 / 4x8 / 16x2, persistent or not, links or terrain
+ * first, 8, 10 or 12 blocks per SM), times them with CUDA events on `stream`, keeps the fastest on the
  * view and returns it with its mean time per render.  Synchronises; for setup, not the hot loop. */
 RPL_API rpl_status rpl_view_autotune(rpl_view_t view, const float *link_poses, int64_t step,
                                      int64_t env_offset, void *depth_out, void *stream, int32_t reps,
@@ -347,6 +347,20 @@ RPL_API void rpl_server_destroy(rpl_server_t server);
  * (last rendered step + 1); with no mask the next render must use `step`.  Asynchronous on
  * `stream`.  Errors: INVALID_ARG, CUDA. */
 RPL_API rpl_status rpl_view_reset(rpl_view_t view, const uint8_t *env_mask, int64_t step, void *stream);
+
+/* Checkpoint of the sensor state, so that a trainer resumes bit-exact (the paper does not describe
+ * checkpointing; this serves callers of the library).  The state is the last rendered step, each
+ * env's first step since its reset, and the latency ring ([n_envs, max_latency + 1, pixels per
+ * env] float32, absent when max_latency is 0): a 64-byte header (magic "RPLS", version, n_envs,
+ * pixels per env, ring span, flags, last step), then n_envs int64 first steps, then the ring.
+ * rpl_view_state_size gives the byte count; rpl_view_state_get waits for the view's work and
+ * copies the state into buf (host or device, `bytes` >= the size); rpl_view_state_set loads it
+ * into a view with the same n_envs, pixels per env and max_latency (cameras, sensor and mounts
+ * are configuration, set by their own calls), after which rendering continues from the saved step.
+ * Errors: INVALID_ARG (NULL, too small, a header that does not match the view), CUDA. */
+RPL_API rpl_status rpl_view_state_size(rpl_view_t view, int64_t *bytes);
+RPL_API rpl_status rpl_view_state_get(rpl_view_t view, void *buf, int64_t bytes);
+RPL_API rpl_status rpl_view_state_set(rpl_view_t view, const void *buf, int64_t bytes);
 
 /* Wait until the view's most recently enqueued work (render, reset, graph replay or a server's
  * batch) has finished, on whichever stream it went (the stream may since have been destroyed),

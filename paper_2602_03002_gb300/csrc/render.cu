@@ -288,10 +288,11 @@ __device__ __forceinline__ void make_ray(Ray &r, float3 base, float3 off, float3
     r.kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
     const int kx = r.kz == 2 ? 0 : r.kz + 1;
     const int ky = kx == 2 ? 0 : kx + 1;
-    const float dz = comp(d, r.kz);
-    r.Sx = comp(d, kx) / dz;
-    r.Sy = comp(d, ky) / dz;
-    r.Sz = 1.0f / dz;
+    // the shear only has to be the same for every triangle of this ray (watertightness), not the
+    // correctly rounded quotient, so d_k / d_z is a product with the reciprocal
+    r.Sz = 1.0f / comp(d, r.kz);
+    r.Sx = comp(d, kx) * r.Sz;
+    r.Sy = comp(d, ky) * r.Sz;
 }
 
 // Slab test of one child box against (0, tmax]; returns the entry distance or +inf.
@@ -367,30 +368,29 @@ constexpr int kDone = INT_MIN;
 
 __device__ __forceinline__ int leaf_ref(int child, int count) { return ~((~child << 3) | (count - 1)); }
 
+__device__ __forceinline__ int stack_pop(const int *stack, int &sp) { return sp > 0 ? stack[--sp] : kDone; }
+
 // Closest hit below tmax in one BVH; tmax shrinks to the hit distance.  Returns false when the stack
 // would overflow (never for scenes accepted at build time).
 //
 // Inner nodes and leaves are handled in two phases (Aila and Laine, "Understanding the Efficiency of
 // Ray Traversal on GPUs", HPG 2009): a lane that meets a leaf postpones it and keeps descending
 // while any lane of the warp has not found a leaf yet, then the warp tests its leaves together, so
-// triangle tests run with most lanes active instead of one lane at a time.
+// triangle tests run with most lanes active instead of one lane at a time.  The stack (in local
+// memory, cached in L1) holds node references only: culling popped entries by their entry distance
+// cost more than the node fetches it saves, which mostly hit in cache.  (Measured alternatives that
+// were slower on the scale workload: a shared-memory short stack, whose carve-out takes L1 capacity
+// the node fetches depend on; one traversal loop shared by links and terrain; and compacting the
+// warp's (ray, link) pairs so that link BVHs are traversed with full warps.)
 template <bool kSplit, bool kCount>
 __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const float4 *__restrict__ tris, int root,
                                          const Ray &r, float &tmax, bool &hit, Counts &cnt) {
     int stack_node[kStackDepth];
-    float stack_t[kStackDepth];
     int sp = 0;
     bool ok = true;
     int cur = root;      // >= 0 inner node, < 0 leaf reference, kDone nothing left
     int pending = 0;     // postponed leaf reference, 0 = none
-    // the nearest pending entry that still starts before the bound
-    auto pop = [&]() -> int {
-        while (sp > 0) {
-            --sp;
-            if (stack_t[sp] <= tmax) return stack_node[sp];
-        }
-        return kDone;
-    };
+    auto pop = [&]() -> int { return stack_pop(stack_node, sp); };
 #pragma unroll 1
     for (;;) {
 #pragma unroll 1
@@ -418,9 +418,7 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
                     cur = kDone;
                     break;
                 }
-                stack_node[sp] = first0 ? e1 : e0;
-                stack_t[sp] = first0 ? t1 : t0;
-                ++sp;
+                stack_node[sp++] = first0 ? e1 : e0;
                 cur = first0 ? e0 : e1;
             } else if (h0) {
                 cur = e0;
@@ -802,8 +800,8 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
 }
 
 // kMinBlocks caps registers so that many blocks of 128 threads stay resident per SM (8 -> 64
-// registers, 12 -> 40).  With p.persistent the grid holds only as many blocks as fit on the device
-// at once and each warp walks the tiles with a grid stride; otherwise one warp per tile.
+// registers, 10 -> 48, 12 -> 40).  With p.persistent the grid holds only as many blocks as fit on
+// the device at once and each warp walks the tiles with a grid stride; otherwise one warp per tile.
 template <bool kCount, bool kWide, int kMinBlocks>
 __global__ void __launch_bounds__(128, kMinBlocks) render_kernel(const __grid_constant__ RenderParams p) {
     const int lane = threadIdx.x & 31;
@@ -883,7 +881,7 @@ cudaError_t launch_prep(const PrepParams &p, cudaStream_t s) {
 cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
     const int64_t warps = (int64_t)p.E * p.tiles_per_env;
     if (warps == 0) return cudaSuccess;
-    const int min_blocks = p.min_blocks == 12 ? 12 : 8;
+    const int min_blocks = p.min_blocks == 12 ? 12 : (p.min_blocks == 10 ? 10 : 8);
     int64_t blocks = (warps + 3) / 4;
     if (p.persistent) {
         int dev = 0, sms = 0;
@@ -903,6 +901,11 @@ cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
             render_kernel<false, true, 12><<<g, 128, 0, s>>>(p);
         else
             render_kernel<false, false, 12><<<g, 128, 0, s>>>(p);
+    } else if (min_blocks == 10) {
+        if (p.wide)
+            render_kernel<false, true, 10><<<g, 128, 0, s>>>(p);
+        else
+            render_kernel<false, false, 10><<<g, 128, 0, s>>>(p);
     } else {
         if (p.wide)
             render_kernel<false, true, 8><<<g, 128, 0, s>>>(p);
@@ -929,7 +932,7 @@ cudaError_t launch_render_multi(const RenderParams *reqs_dev, const int64_t *pre
                                 int64_t total_warps, bool wide, int min_blocks, bool persistent, cudaStream_t s) {
     if (total_warps <= 0 || n_req <= 0) return cudaSuccess;
     int64_t blocks = (total_warps + 3) / 4;
-    const int mb = min_blocks == 12 ? 12 : 8;
+    const int mb = min_blocks == 12 ? 12 : (min_blocks == 10 ? 10 : 8);
     if (persistent) {
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
@@ -941,11 +944,15 @@ cudaError_t launch_render_multi(const RenderParams *reqs_dev, const int64_t *pre
     if (wide) {
         if (mb == 12)
             render_multi_kernel<true, 12><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
+        else if (mb == 10)
+            render_multi_kernel<true, 10><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
         else
             render_multi_kernel<true, 8><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
     } else {
         if (mb == 12)
             render_multi_kernel<false, 12><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
+        else if (mb == 10)
+            render_multi_kernel<false, 10><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
         else
             render_multi_kernel<false, 8><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
     }

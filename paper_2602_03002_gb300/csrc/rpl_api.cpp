@@ -1,6 +1,7 @@
 // rpl_api.cpp -- the C ABI (include/rpl.h): scenes, views, argument checks, device memory,
 // host/device pointer handling and kernel launches.  No torch types cross this boundary.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -38,6 +39,15 @@ rpl_status cuda_fail(cudaError_t e, const char *what) {
     return fail(e == cudaErrorMemoryAllocation ? RPL_ERR_OUT_OF_MEMORY : RPL_ERR_CUDA, "%s: %s", what,
                 cudaGetErrorString(e));
 }
+
+// An NVTX range around one library call, so profiler timelines show the calls (free when no tool
+// is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Makes `dev` current for the lifetime of the guard and restores the caller's device after.
 struct DeviceGuard {
@@ -188,6 +198,7 @@ RPL_API const char *rpl_last_error(void) { return g_err.c_str(); }
 
 RPL_API rpl_status rpl_scene_create(const float *verts, int64_t n_verts, const int32_t *tris, int64_t n_tris,
                                     const rpl_scene_opts *opts, rpl_scene_t *out) {
+    NvtxRange range("rpl_scene_create");
     if (!out) return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: out is NULL");
     *out = nullptr;
     if (n_verts < 0 || n_tris < 0) return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: negative size");
@@ -827,6 +838,7 @@ static rpl_status check_render_args(rpl_view *v, const float *poses, int64_t env
 
 RPL_API rpl_status rpl_render(rpl_view_t v, const float *poses, int64_t step, int64_t env_offset, void *out,
                               void *stream) {
+    NvtxRange range("rpl_render");
     rpl_status st = check_render_args(v, poses, env_offset, out);
     if (st != RPL_OK) return st;
     if (v->has_last && step != v->last_step && step != v->last_step + 1)
@@ -945,6 +957,87 @@ RPL_API rpl_status rpl_view_reset(rpl_view_t v, const uint8_t *mask, int64_t ste
     return RPL_OK;
 }
 
+namespace {
+
+struct StateHeader {
+    char magic[4];           // "RPLS"
+    int32_t version;         // 1
+    int32_t E, P, span;
+    int32_t flags;           // bit 0 has_last, bit 1 need_first
+    int64_t last_step;
+    int64_t reserved[4];
+};
+static_assert(sizeof(StateHeader) == 64, "state header is 64 bytes");
+
+int64_t state_bytes(const rpl_view *v) {
+    const int64_t span = (int64_t)v->sensor.max_latency + 1;
+    const int64_t ring = span > 1 && v->cams_set ? (int64_t)v->E * span * v->P * (int64_t)sizeof(float) : 0;
+    return (int64_t)sizeof(StateHeader) + (int64_t)v->E * (int64_t)sizeof(int64_t) + ring;
+}
+
+}  // namespace
+
+RPL_API rpl_status rpl_view_state_size(rpl_view_t v, int64_t *bytes) {
+    if (!v || !bytes) return fail(RPL_ERR_INVALID_ARG, "rpl_view_state_size: NULL argument");
+    if (!v->cams_set) return fail(RPL_ERR_INVALID_ARG, "rpl_view_state_size: cameras not set");
+    *bytes = state_bytes(v);
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_view_state_get(rpl_view_t v, void *buf, int64_t bytes) {
+    if (!v || !buf) return fail(RPL_ERR_INVALID_ARG, "rpl_view_state_get: NULL argument");
+    if (!v->cams_set) return fail(RPL_ERR_INVALID_ARG, "rpl_view_state_get: cameras not set");
+    const int64_t need = state_bytes(v);
+    if (bytes < need) return fail(RPL_ERR_INVALID_ARG, "rpl_view_state_get: buffer of %lld bytes, need %lld",
+                                  (long long)bytes, (long long)need);
+    DeviceGuard g(v->scene->device);
+    if (v->has_done) cudaEventSynchronize(v->done);
+    StateHeader h{};
+    std::memcpy(h.magic, "RPLS", 4);
+    h.version = 1;
+    h.E = v->E;
+    h.P = (int32_t)v->P;
+    h.span = v->sensor.max_latency + 1;
+    h.flags = (v->has_last ? 1 : 0) | (v->need_first ? 2 : 0);
+    h.last_step = v->last_step;
+    char *dst = static_cast<char *>(buf);
+    cudaError_t e = cudaMemcpy(dst, &h, sizeof h, cudaMemcpyDefault);
+    const size_t sf = (size_t)v->E * sizeof(int64_t);
+    if (e == cudaSuccess && sf) e = cudaMemcpy(dst + sizeof h, v->s_first.p, sf, cudaMemcpyDefault);
+    const size_t ring = (size_t)(need - (int64_t)sizeof h - (int64_t)sf);
+    if (e == cudaSuccess && ring) e = cudaMemcpy(dst + sizeof h + sf, v->ring.p, ring, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_view_state_get: copying the state");
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_view_state_set(rpl_view_t v, const void *buf, int64_t bytes) {
+    if (!v || !buf) return fail(RPL_ERR_INVALID_ARG, "rpl_view_state_set: NULL argument");
+    if (!v->cams_set) return fail(RPL_ERR_INVALID_ARG, "rpl_view_state_set: cameras not set");
+    const int64_t need = state_bytes(v);
+    if (bytes < need) return fail(RPL_ERR_INVALID_ARG, "rpl_view_state_set: %lld bytes, the state has %lld",
+                                  (long long)bytes, (long long)need);
+    DeviceGuard g(v->scene->device);
+    StateHeader h{};
+    const char *src = static_cast<const char *>(buf);
+    cudaError_t e = cudaMemcpy(&h, src, sizeof h, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_view_state_set: reading the header");
+    if (std::memcmp(h.magic, "RPLS", 4) != 0 || h.version != 1 || h.E != v->E || h.P != (int32_t)v->P ||
+        h.span != v->sensor.max_latency + 1)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_view_state_set: the state was saved from a view with other envs, "
+                                         "pixels or latency span");
+    if (v->has_done) cudaEventSynchronize(v->done);   // an enqueued render may still use the ring
+    const size_t sf = (size_t)v->E * sizeof(int64_t);
+    if (sf) e = cudaMemcpy(v->s_first.p, src + sizeof h, sf, cudaMemcpyDefault);
+    const size_t ring = (size_t)(need - (int64_t)sizeof h - (int64_t)sf);
+    if (e == cudaSuccess && ring) e = cudaMemcpy(v->ring.p, src + sizeof h + sf, ring, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_view_state_set: copying the state");
+    v->has_last = (h.flags & 1) != 0;
+    v->need_first = (h.flags & 2) != 0;
+    v->last_step = h.last_step;
+    v->dev_step_next = INT64_MIN;   // a graph replay resets its device step counter
+    return RPL_OK;
+}
+
 RPL_API rpl_status rpl_sync(rpl_view_t v) {
     if (!v) return fail(RPL_ERR_INVALID_ARG, "rpl_sync: view is NULL");
     DeviceGuard g(v->scene->device);
@@ -989,7 +1082,8 @@ RPL_API rpl_status rpl_view_kernel_ms(rpl_view_t v, float *ms, int32_t max_n, in
 
 static bool tuning_from(const rpl_tuning *t, Tuning *out) {
     const int lg = t->tile_w == 4 ? 2 : t->tile_w == 8 ? 3 : t->tile_w == 16 ? 4 : -1;
-    if (lg < 0 || t->tile_w * t->tile_h != 32 || (t->min_blocks != 8 && t->min_blocks != 12)) return false;
+    if (lg < 0 || t->tile_w * t->tile_h != 32 || (t->min_blocks != 8 && t->min_blocks != 10 && t->min_blocks != 12))
+        return false;
     out->tile_w_log2 = lg;
     out->persistent = t->persistent ? 1 : 0;
     out->terrain_first = t->terrain_first ? 1 : 0;
@@ -1009,7 +1103,7 @@ RPL_API rpl_status rpl_view_tuning_set(rpl_view_t v, const rpl_tuning *t) {
     if (!v || !t) return fail(RPL_ERR_INVALID_ARG, "rpl_view_tuning_set: NULL argument");
     Tuning n;
     if (!tuning_from(t, &n))
-        return fail(RPL_ERR_INVALID_ARG, "rpl_view_tuning_set: tile must be 4x8, 8x4 or 16x2 and min_blocks 8 or 12");
+        return fail(RPL_ERR_INVALID_ARG, "rpl_view_tuning_set: tile must be 4x8, 8x4 or 16x2 and min_blocks 8, 10 or 12");
     v->tune = n;
     return RPL_OK;
 }
@@ -1022,6 +1116,7 @@ RPL_API rpl_status rpl_view_tuning_get(rpl_view_t v, rpl_tuning *t) {
 
 RPL_API rpl_status rpl_view_autotune(rpl_view_t v, const float *poses, int64_t step, int64_t env_offset, void *out,
                                      void *stream, int32_t reps, rpl_tuning *best, float *best_ms) {
+    NvtxRange range("rpl_view_autotune");
     rpl_status st = check_render_args(v, poses, env_offset, out);
     if (st != RPL_OK) return st;
     if (reps < 1) return fail(RPL_ERR_INVALID_ARG, "rpl_view_autotune: reps must be >= 1");
@@ -1053,8 +1148,8 @@ RPL_API rpl_status rpl_view_autotune(rpl_view_t v, const float *poses, int64_t s
     for (int ti = 0; ti < 3 && st == RPL_OK; ++ti)
         for (int pers = 0; pers < 2 && st == RPL_OK; ++pers)
             for (int tf = 0; tf < 2 && st == RPL_OK; ++tf)
-                for (int mb = 0; mb < 2 && st == RPL_OK; ++mb) {
-                    v->tune = Tuning{tiles[ti], pers, tf, mb ? 12 : 8};
+                for (int mb = 8; mb <= 12 && st == RPL_OK; mb += 2) {
+                    v->tune = Tuning{tiles[ti], pers, tf, mb};
                     st = enqueue(v, poses, step, env_offset, out, cs, false, nullptr);   // warm-up
                     if (st != RPL_OK) break;
                     cudaEventRecord(a, cs);
@@ -1090,6 +1185,7 @@ static void graph_release(rpl_view *v) {
 
 RPL_API rpl_status rpl_render_graph(rpl_view_t v, const float *poses, int64_t env_offset, void *out, void *stream,
                                     int64_t *step_out) {
+    NvtxRange range("rpl_render_graph");
     rpl_status st = check_render_args(v, poses, env_offset, out);
     if (st != RPL_OK) return st;
     const int64_t next = v->has_last ? v->last_step + 1 : 0;

@@ -8,6 +8,7 @@
 // when the launch's event has passed.  Batches on different slots overlap on the device, so
 // requests that arrive while others run are admitted as soon as a slot and memory free up.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -136,6 +137,7 @@ namespace {
 
 // Fills slot s with the admitted batch and launches it (called without the server lock).
 void launch_batch(rpl_server *sv, Slot &s) {
+    nvtxRangePushA("rpl_server_batch");
     cudaStream_t st = s.stream;
     const int n = (int)s.reqs.size();
     int64_t total = 0;
@@ -187,6 +189,7 @@ void launch_batch(rpl_server *sv, Slot &s) {
         cudaGetLastError();
         cudaEventRecord(s.done, st);
     }
+    nvtxRangePop();
 }
 
 void release_staging(rpl_server *sv, Request *r) {
@@ -324,9 +327,9 @@ RPL_API rpl_status rpl_server_create(rpl_scene_t scene, const rpl_server_opts *o
     if (o.staging_bytes == 0) o.staging_bytes = (int64_t)256 << 20;
     if (o.min_blocks == 0) o.min_blocks = 8;
     if (o.max_batch < 1 || o.max_batch > 64 || o.n_streams < 1 || o.n_streams > 8 || o.staging_bytes < 0 ||
-        (o.min_blocks != 8 && o.min_blocks != 12))
+        (o.min_blocks != 8 && o.min_blocks != 10 && o.min_blocks != 12))
         return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_create: max_batch 1..64, n_streams 1..8, "
-                                                "staging_bytes >= 0, min_blocks 8 or 12");
+                                                "staging_bytes >= 0, min_blocks 8, 10 or 12");
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
     cudaSetDevice(si.device);

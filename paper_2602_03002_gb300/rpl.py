@@ -85,7 +85,8 @@ class rpl_counters(ctypes.Structure):
 
 
 EXPORTS = ["rpl_bvh_build_host", "rpl_bvh8_build_host", "rpl_scene_create", "rpl_link_mesh_add", "rpl_scene_info_get", "rpl_scene_destroy", "rpl_view_create",
-           "rpl_cameras_set", "rpl_cameras_randomize", "rpl_side_mask_set", "rpl_sensor_set", "rpl_view_layout", "rpl_render", "rpl_view_reset", "rpl_sync",
+           "rpl_cameras_set", "rpl_cameras_randomize", "rpl_side_mask_set", "rpl_sensor_set", "rpl_view_state_size",
+           "rpl_view_state_get", "rpl_view_state_set", "rpl_view_layout", "rpl_render", "rpl_view_reset", "rpl_sync",
            "rpl_render_counters", "rpl_view_timing", "rpl_view_kernel_ms", "rpl_view_destroy", "rpl_last_error",
            "rpl_version", "rpl_render_static_scratch", "rpl_view_tuning_set", "rpl_view_tuning_get",
            "rpl_view_autotune", "rpl_render_graph", "rpl_server_create", "rpl_server_submit", "rpl_server_wait",
@@ -118,6 +119,9 @@ def lib() -> ctypes.CDLL:
         "rpl_view_layout": ([P, P, P], I32),
         "rpl_render": ([P, P, I64, I64, P, P], I32),
         "rpl_view_reset": ([P, P, I64, P], I32),
+        "rpl_view_state_size": ([P, P], I32),
+        "rpl_view_state_get": ([P, P, I64], I32),
+        "rpl_view_state_set": ([P, P, I64], I32),
         "rpl_sync": ([P], I32),
         "rpl_render_counters": ([P, P, I64, I64, P, P, P], I32),
         "rpl_view_timing": ([P, I32], I32),
@@ -251,6 +255,27 @@ def rpl_cameras_set(view: int, cams: Sequence, per_env_intrinsics=None):
     _check(lib().rpl_cameras_set(view, arr, len(cams), _ptr(intr)))
 
 
+def rpl_view_state_size(view: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib().rpl_view_state_size(view, ctypes.byref(n)))
+    return int(n.value)
+
+
+def rpl_view_state_get(view: int, buf=None):
+    """Sensor-state checkpoint into `buf` (numpy uint8 or torch tensor); a new host array when None."""
+    n = rpl_view_state_size(view)
+    if buf is None:
+        buf = np.empty(n, np.uint8)
+    nbytes = buf.nbytes if isinstance(buf, np.ndarray) else buf.numel() * buf.element_size()
+    _check(lib().rpl_view_state_get(view, _ptr(buf), nbytes))
+    return buf
+
+
+def rpl_view_state_set(view: int, buf):
+    nbytes = buf.nbytes if isinstance(buf, np.ndarray) else buf.numel() * buf.element_size()
+    _check(lib().rpl_view_state_set(view, _ptr(buf), nbytes))
+
+
 def rpl_cameras_randomize(view: int, mount_delta=None):
     """mount_delta: None or [E, C, 7] (dp xyz, dq xyzw), numpy or torch (host or device)."""
     if isinstance(mount_delta, np.ndarray):
@@ -340,7 +365,7 @@ def rpl_view_tuning_get(view: int) -> dict:
 
 
 def rpl_view_autotune(view: int, poses, step: int, env_offset: int, out, stream=None, reps: int = 3):
-    """Times the 24 launch shapes, keeps the fastest on the view; returns (tuning dict, ms per render)."""
+    """Times the 36 launch shapes, keeps the fastest on the view; returns (tuning dict, ms per render)."""
     t = rpl_tuning()
     ms = ctypes.c_float()
     _check(lib().rpl_view_autotune(view, _ptr(poses), int(step), int(env_offset), _ptr(out), _stream_handle(stream),
@@ -425,6 +450,13 @@ class View:
     def set_cameras(self, cams, per_env_intrinsics=None):
         rpl_cameras_set(self.h, cams, per_env_intrinsics)
         self.cams = list(cams)
+
+    def save_state(self, buf=None):
+        """Checkpoint of the sensor state (latency ring, first steps, last step); see rpl_view_state_get."""
+        return rpl_view_state_get(self.h, buf)
+
+    def load_state(self, buf):
+        rpl_view_state_set(self.h, buf)
 
     def randomize_cameras(self, mount_delta=None):
         """Per-env camera mount perturbation [E, C, 7] (dp xyz, dq xyzw), or None to clear."""

@@ -1,7 +1,7 @@
 """Batching: uneven cameras in one launch, launch shapes chosen by the autotuner, graph replay.
 
 The launch shape (tile of 32 rays, persistent grid-stride loop, query order, registers per thread)
-must never change the depth: every one of the 24 shapes gives bit-identical frames, also on ragged
+must never change the depth: every one of the 36 shapes gives bit-identical frames, also on ragged
 cameras where tiles hang over the image edge.  Replaying the captured graph of the whole path must
 continue the sensor history exactly like step-by-step rpl_render calls.
 """
@@ -17,7 +17,7 @@ from paper_2602_03002_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 SHAPES = [dict(tile_w=tw, tile_h=32 // tw, persistent=p, terrain_first=tf, min_blocks=mb)
-          for tw, p, tf, mb in itertools.product((8, 4, 16), (0, 1), (0, 1), (8, 12))]
+          for tw, p, tf, mb in itertools.product((8, 4, 16), (0, 1), (0, 1), (8, 10, 12))]
 
 
 def _ragged(w):
