@@ -460,7 +460,7 @@ def run_serving(args):
     service = float(np.mean(times))
     load = 0.8
     rate = load / service                       # requests per second, all trainers together
-    n_req = max(40, args.steps * 4)
+    n_req = max(400, args.steps * 8)
     sched = []
     for tr in range(n_tr):
         gaps = rng.exponential(n_tr / rate, size=n_req // n_tr)

@@ -833,6 +833,17 @@ __global__ void __launch_bounds__(128, kMinBlocks)
         const RenderParams &p = reqs[lo];
         const int64_t step = p.step_dev ? *p.step_dev : p.step;
         render_tile<false, kWide>(p, warp - prefix[lo], lane, step);
+        if (p.done_counter) {
+            // per-request completion inside the fused launch: every lane's stores are made visible,
+            // then the warp counts its tile off; the warp that finishes the request's last tile
+            // raises the request's flag in host-mapped memory (the last-block pattern)
+            __threadfence();
+            __syncwarp();
+            if (lane == 0 && atomicSub(p.done_counter, 1) == 1) {
+                __threadfence_system();
+                *reinterpret_cast<volatile int32_t *>(p.done_flag) = 1;
+            }
+        }
     }
 }
 

@@ -89,6 +89,10 @@ struct RenderParams {
     void *out;                      // [E, pix_per_env] of out_dtype
     int32_t *err;                   // error word (bit 0: traversal stack overflow)
     unsigned long long *counters;   // rpl_counters fields, or null
+    // fused launches only (render_multi_kernel): tiles of this request still running, and a word in
+    // host-mapped memory set to 1 when the last of them has stored its pixels; null when unused
+    int32_t *done_counter;
+    int32_t *done_flag;
 };
 
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s);

@@ -1310,10 +1310,12 @@ rpl_status view_prepare(rpl_view *v, const float *poses_dev, int64_t step, int64
 }
 
 void view_commit(rpl_view *v, int64_t step, cudaStream_t st) {
+    (void)st;
     v->has_last = true;
     v->last_step = step;
-    mark_done(v, st);
 }
+
+void view_mark_done(rpl_view *v, cudaStream_t st) { mark_done(v, st); }
 
 size_t view_pose_bytes(const rpl_view *v) { return (size_t)v->E * v->L * 7 * sizeof(float); }
 size_t view_out_bytes(const rpl_view *v) { return (size_t)v->E * v->P * out_elem_bytes(v); }

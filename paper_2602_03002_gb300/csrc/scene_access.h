@@ -28,7 +28,10 @@ rpl_status view_validate(rpl_view *v, const float *poses, int64_t env_offset, vo
 bool view_step_allowed(const rpl_view *v, int64_t step);
 rpl_status view_prepare(rpl_view *v, const float *poses_dev, int64_t step, int64_t env_offset, void *out_dev,
                         cudaStream_t st, RenderParams *rp, int64_t *warps);
+// Records that `step` is the view's last rendered step (its work enqueued on `st`).
 void view_commit(rpl_view *v, int64_t step, cudaStream_t st);
+// Marks the end of the view's enqueued work on `st` (recorded after the render that uses it).
+void view_mark_done(rpl_view *v, cudaStream_t st);
 size_t view_pose_bytes(const rpl_view *v);
 size_t view_out_bytes(const rpl_view *v);
 int32_t view_envs(const rpl_view *v);

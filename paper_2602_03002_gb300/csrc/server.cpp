@@ -7,6 +7,10 @@
 // launch per request, then one render launch over the tiles of all of them -- and completes them
 // when the launch's event has passed.  Batches on different slots overlap on the device, so
 // requests that arrive while others run are admitted as soon as a slot and memory free up.
+// Inside a fused launch the requests are ordered by size, smallest first, and a request whose
+// buffers are on the device completes as soon as its own tiles are done: the kernel counts them off
+// and raises a flag in host-mapped memory that the worker polls, so a small request fused with a
+// large one does not wait for the large one.
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -96,6 +100,7 @@ struct Request {
     rpl_status status = RPL_OK;
     std::string err;
     bool done = false, cancelled = false;
+    bool early = false;   // completes by its own flag inside the fused launch
 };
 
 struct Slot {
@@ -105,6 +110,10 @@ struct Slot {
     int64_t *h_prefix = nullptr;        // pinned
     RenderParams *d_params = nullptr;
     int64_t *d_prefix = nullptr;
+    int32_t *h_flags = nullptr;         // pinned, mapped: per-request completion flags
+    int32_t *d_flags = nullptr;         // device address of h_flags
+    int32_t *h_remaining = nullptr;     // pinned: tiles per request
+    int32_t *d_remaining = nullptr;     // device: tiles still running per request
     bool busy = false;
     std::vector<Request *> reqs;
 };
@@ -140,10 +149,10 @@ void launch_batch(rpl_server *sv, Slot &s) {
     nvtxRangePushA("rpl_server_batch");
     cudaStream_t st = s.stream;
     const int n = (int)s.reqs.size();
-    int64_t total = 0;
+    std::vector<RenderParams> prm(n);
+    std::vector<int64_t> tiles(n, 0);
     for (int i = 0; i < n; ++i) {
         Request *r = s.reqs[i];
-        s.h_prefix[i] = total;
         const float *pd = r->poses_host ? reinterpret_cast<const float *>(sv->arena_dev + r->pose_off) : r->poses;
         void *od = r->out_host ? (void *)(sv->arena_dev + r->out_off) : r->out;
         if (r->poses_host) {
@@ -155,19 +164,42 @@ void launch_batch(rpl_server *sv, Slot &s) {
             }
         }
         int64_t warps = 0;
-        rpl_status stt = view_prepare(r->view, pd, r->step, r->env_offset, od, st, &s.h_params[i], &warps);
+        rpl_status stt = view_prepare(r->view, pd, r->step, r->env_offset, od, st, &prm[i], &warps);
         if (stt != RPL_OK) {
             r->status = stt;
             r->err = rpl_last_error();
             continue;
         }
         view_commit(r->view, r->step, st);
-        total += warps;
+        tiles[i] = warps;
     }
+    // smallest requests first: the launch's warps run roughly in order, so they finish early
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tiles[a] < tiles[b]; });
+    std::vector<Request *> sorted(n);
+    int64_t total = 0;
+    for (int k = 0; k < n; ++k) {
+        const int i = order[k];
+        Request *r = s.reqs[i];
+        sorted[k] = r;
+        s.h_params[k] = prm[i];
+        s.h_prefix[k] = total;
+        total += tiles[i];
+        // a request with device buffers and no downsampled camera completes by its own flag
+        r->early = r->status == RPL_OK && !r->out_host && prm[i].raw_per_env == 0 && tiles[i] > 0;
+        s.h_flags[k] = 0;
+        s.h_remaining[k] = (int32_t)tiles[i];
+        s.h_params[k].done_counter = r->early ? s.d_remaining + k : nullptr;
+        s.h_params[k].done_flag = r->early ? s.d_flags + k : nullptr;
+    }
+    s.reqs = sorted;
     s.h_prefix[n] = total;
     cudaError_t e = cudaMemcpyAsync(s.d_params, s.h_params, (size_t)n * sizeof(RenderParams), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s.d_prefix, s.h_prefix, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.d_remaining, s.h_remaining, (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = launch_render_multi(s.d_params, s.d_prefix, n, total, sv->wide, sv->opts.min_blocks,
                                 sv->opts.persistent != 0, st);
@@ -178,13 +210,17 @@ void launch_batch(rpl_server *sv, Slot &s) {
         if (r->out_host && r->status == RPL_OK)
             e = cudaMemcpyAsync(r->out, sv->arena_dev + r->out_off, r->out_bytes, cudaMemcpyDeviceToHost, st);
     }
+    for (int i = 0; i < n && e == cudaSuccess; ++i)   // rpl_sync / rpl_view_destroy of a view wait for this
+        if (s.reqs[i]->status == RPL_OK) view_mark_done(s.reqs[i]->view, st);
     if (e == cudaSuccess) e = cudaEventRecord(s.done, st);
     if (e != cudaSuccess) {
-        for (Request *r : s.reqs)
+        for (Request *r : s.reqs) {
+            r->early = false;   // completes with the batch, carrying the error
             if (r->status == RPL_OK) {
                 r->status = RPL_ERR_CUDA;
                 r->err = cudaGetErrorString(e);
             }
+        }
         cudaStreamSynchronize(st);   // let anything that did launch finish before the slot is reused
         cudaGetLastError();
         cudaEventRecord(s.done, st);
@@ -212,15 +248,27 @@ void finish(rpl_server *sv, Request *r, Clock::time_point now) {
     }
 }
 
-// Completes the batches whose event has passed (lock held).
+// Completes the requests whose own flag is up and the batches whose event has passed (lock held).
+// An early-completed request leaves the slot's list (its caller may free it once waited for).
 void poll_slots(rpl_server *sv) {
     bool any = false;
     for (Slot &s : sv->slots) {
         if (!s.busy) continue;
+        for (size_t k = 0; k < s.reqs.size(); ++k) {
+            Request *r = s.reqs[k];
+            if (!r || !r->early || r->cancelled) continue;
+            if (*reinterpret_cast<volatile int32_t *>(s.h_flags + k) == 0) continue;
+            sv->on_gpu.erase(r->view);   // its tiles are done: the view may take its next request
+            release_staging(sv, r);      // staged poses were consumed by the prep kernel
+            finish(sv, r, Clock::now());
+            s.reqs[k] = nullptr;
+            any = true;
+        }
         const cudaError_t q = cudaEventQuery(s.done);
         if (q == cudaErrorNotReady) continue;
         const Clock::time_point now = Clock::now();
         for (Request *r : s.reqs) {
+            if (!r) continue;
             if (q != cudaSuccess && r->status == RPL_OK) {
                 r->status = RPL_ERR_CUDA;
                 r->err = cudaGetErrorString(q);
@@ -349,6 +397,10 @@ RPL_API rpl_status rpl_server_create(rpl_scene_t scene, const rpl_server_opts *o
         if (e == cudaSuccess) e = cudaHostAlloc(&s.h_prefix, (o.max_batch + 1) * sizeof(int64_t), cudaHostAllocDefault);
         if (e == cudaSuccess) e = cudaMalloc(&s.d_params, o.max_batch * sizeof(RenderParams));
         if (e == cudaSuccess) e = cudaMalloc(&s.d_prefix, (o.max_batch + 1) * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaHostAlloc(&s.h_flags, o.max_batch * sizeof(int32_t), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&s.d_flags, s.h_flags, 0);
+        if (e == cudaSuccess) e = cudaHostAlloc(&s.h_remaining, o.max_batch * sizeof(int32_t), cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaMalloc(&s.d_remaining, o.max_batch * sizeof(int32_t));
     }
     if (e != cudaSuccess) {
         rpl_server_destroy(sv);
@@ -488,6 +540,9 @@ RPL_API void rpl_server_destroy(rpl_server_t sv) {
         if (s.h_prefix) cudaFreeHost(s.h_prefix);
         if (s.d_params) cudaFree(s.d_params);
         if (s.d_prefix) cudaFree(s.d_prefix);
+        if (s.h_flags) cudaFreeHost(s.h_flags);
+        if (s.h_remaining) cudaFreeHost(s.h_remaining);
+        if (s.d_remaining) cudaFree(s.d_remaining);
     }
     if (sv->arena_dev) cudaFree(sv->arena_dev);
     for (auto &kv : sv->tickets) delete kv.second;

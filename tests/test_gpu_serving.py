@@ -180,3 +180,39 @@ def test_trainer_that_dies_mid_request_leaves_the_server_serving(cuda, rpl_lib):
     st = server.stats()
     assert st["completed"] >= 3 and st["failed"] == 0
     server.close()   # the abandoned request is drained and freed
+
+
+def test_small_request_fused_with_a_large_one_completes_first(cuda, rpl_lib):
+    """Inside one fused launch the smaller request's tiles run first and it completes by its own flag,
+    before the launch ends; both results equal their renders alone."""
+    torch = cuda
+    w = _workload()
+    scene = rpl_lib.Scene.from_workload(w)
+    big_w = W.config_small(n_steps=1, n_envs=16384)
+    blocker = rpl_lib.View(scene, 4096, w.n_links)
+    blocker.set_cameras(w.cameras)
+    vb = rpl_lib.View(scene, 16384, w.n_links)
+    vb.set_cameras(w.cameras)
+    vb.set_sensor(SENSOR)
+    pb = torch.from_numpy(np.ascontiguousarray(big_w.poses[0])).cuda()
+    (vs, ps, E, C), = _views(rpl_lib, torch, w, scene, [(3, 2)])
+    alone_big = vb.render(pb, 0).clone()
+    alone_small = vs.render(ps[0], 0, 9).clone()
+    torch.cuda.synchronize()
+    vb2 = rpl_lib.View(scene, 16384, w.n_links)
+    vb2.set_cameras(w.cameras)
+    vb2.set_sensor(SENSOR)
+    (vs2, _, _, _), = _views(rpl_lib, torch, w, scene, [(3, 2)])
+    server = rpl_lib.Server(scene, max_batch=8, n_streams=1)
+    ob, os_ = vb2.out_tensor(), vs2.out_tensor()
+    t0 = server.submit(blocker, pb[:4096], 0, blocker.out_tensor())   # occupies the only slot
+    tb = server.submit(vb2, pb, 0, ob)
+    ts = server.submit(vs2, ps[0], 0, os_, 9)
+    lat_s = server.wait(ts)
+    lat_b = server.wait(tb)
+    server.wait(t0)
+    st = server.stats()
+    server.close()
+    assert torch.equal(ob, alone_big) and torch.equal(os_, alone_small)
+    assert st["max_batch_seen"] >= 2, st          # the two were fused
+    assert lat_s < lat_b, (lat_s, lat_b)
