@@ -520,3 +520,42 @@ def test_side_masking_columns_values_and_key():
     mm = sc.render([big], poses, step, r, sen, rsm_mode=np.full(E, 2, np.uint8), rsm_cols=(0, 0, 32), flags=False)
     u = (mm["depth"] - np.float32(big.d_min)) / (np.float32(big.d_max) - np.float32(big.d_min))
     assert stats.kstest(u, "uniform").pvalue > 1e-4
+
+
+def test_mirrored_scene_gives_the_mirrored_image():
+    """Reflecting the whole small workload in the plane y = 0 (terrain, link meshes in their frames,
+    link poses, camera mounts) mirrors every image left-right: with the principal point at the image
+    centre, pixel x of the mirrored render equals pixel W-1-x of the original.  Link poses reflect as
+    q -> (-qx, qy, -qz, qw); a mount rotation as R -> M R F with F flipping the optical x axis."""
+    w = W.config_small(n_steps=1, n_envs=3)
+    base = _render((w.terrain_verts, w.terrain_tris), list(zip(w.link_verts, w.link_tris)), w.cameras, w.poses[0])
+    M = np.diag([1.0, -1.0, 1.0])
+    F = np.diag([-1.0, 1.0, 1.0])
+    tv = (w.terrain_verts.astype(np.float64) @ M).astype(np.float32)
+    lv = [(v.astype(np.float64) @ M).astype(np.float32) for v in w.link_verts]
+    poses = w.poses[0].copy()
+    poses[..., 1] = -poses[..., 1]
+    poses[..., 3] = -poses[..., 3]
+    poses[..., 5] = -poses[..., 5]
+    cams = []
+    for c in w.cameras:
+        R = Rotation.from_quat(_f32(c.offset_quat)).as_matrix()
+        q = Rotation.from_matrix(M @ R @ F).as_quat()
+        cams.append(W.Camera(c.width, c.height, c.fx, c.fy, c.cx, c.cy, c.mount_link,
+                             (c.offset_pos[0], -c.offset_pos[1], c.offset_pos[2]), tuple(q), c.d_min, c.d_max))
+    mir = _render((tv, w.terrain_tris), list(zip(lv, w.link_tris)), cams, poses)
+    n = 0
+    for e in range(w.n_envs):
+        for k, c in enumerate(w.cameras):
+            off = e * sum(x.width * x.height for x in w.cameras) + sum(x.width * x.height for x in w.cameras[:k])
+            sl = slice(off, off + c.width * c.height)
+            a = base["depth"][sl].reshape(c.height, c.width)
+            b = mir["depth"][sl].reshape(c.height, c.width)[:, ::-1]
+            fa = base["flags"][sl].reshape(c.height, c.width)
+            fb = mir["flags"][sl].reshape(c.height, c.width)[:, ::-1]
+            edge = ((fa | fb) & oracle.FLAG_EDGE) != 0
+            d = np.abs(a - b)[~edge]
+            assert d.max() < 2e-6, d.max()             # float32 rounding of the reflected mount only
+            n += d.size
+            assert not np.array_equal(a, a[:, ::-1])   # the images are not symmetric themselves
+    assert n > 0.99 * base["depth"].size
