@@ -233,12 +233,15 @@ RPL_API rpl_status rpl_view_layout(rpl_view_t view, int64_t *cam_offsets, int64_
  *   env_offset  global id of env 0 of this view (keys the random streams, so that a range of envs
  *               rendered by another GPU or process draws the same numbers); env_offset + n_envs
  *               must not exceed 2^32
- *   depth_out   host or device, n_envs * total_per_env float32 (see rpl_view_layout)
+ *   depth_out   host or device, n_envs * total_per_env elements of the view's output type
+ *               (float32, or 16-bit for RPL_OUT_F16 / RPL_OUT_U16; see rpl_view_layout)
  *   stream      cudaStream_t to run on (NULL = the legacy default stream)
  * With device buffers the call only enqueues work and returns; it does not allocate or
  * synchronise, so it can be captured into a CUDA graph (a captured graph replays the step it was
- * captured with).  With a host buffer the poses are staged through view-owned device memory
- * (allocated on the first such call) and the call returns after the depth is in depth_out.
+ * captured with).  Host buffers are staged through view-owned device memory (allocated on the
+ * first such call): with a host depth_out the call returns after the depth is in depth_out; with
+ * host poses and a device depth_out it returns after enqueuing, and pinned host poses are read
+ * asynchronously, so they must stay unchanged until the stream has passed this render.
  * Errors: INVALID_ARG, CUDA, DEVICE_FAULT (an earlier launch on this view recorded a kernel
  * error; call rpl_sync to read it and clear it). */
 RPL_API rpl_status rpl_render(rpl_view_t view, const float *link_poses, int64_t step,
