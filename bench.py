@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default=None,
                     help="fixed launch shape tile_w,tile_h,persistent,terrain_first,min_blocks (skips the autotuner)")
+    ap.add_argument("--bvh", type=int, default=None, choices=[2, 4, 8],
+                    help="terrain BVH layout: 2 binary, 4 four-wide FP32, 8 eight-wide quantised "
+                         "(default: 8 for precision, else 2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the oracle sample")
@@ -77,16 +80,30 @@ def workload(args, rank):
     return w
 
 
-def workload_name(w, variant):
+def bvh_number(args):
+    if args.bvh is not None:
+        return args.bvh
+    return 8 if args.variant == "precision" else 2
+
+
+def bvh_kind(args, rpl):
+    return {2: rpl.RPL_BVH2, 4: rpl.RPL_BVH4, 8: rpl.RPL_BVH8Q8}[bvh_number(args)]
+
+
+BVH_NAMES = {2: "binary BVH", 4: "four-wide FP32 BVH", 8: "eight-wide BVH with 8-bit quantised boxes"}
+
+
+def workload_name(w, variant, bvh):
     cams = " + ".join("%dx%d" % (c.width, c.height) + ("->%dx%d" % (c.out_width, c.out_height) if c.downsample > 1 else "")
                       for c in w.cameras)
     s = w.sensor
     sensor = ("sensor sigma %.2f m + %.2f depth, %.0f%% dropout, latency 0-%d steps"
               % (s.sigma_abs, s.sigma_rel, 100 * s.p_drop, s.max_latency) if s.enabled else "no sensor model")
-    form = {"plain": "binary BVH, FP32 depth", "precision": "8-wide BVH with 8-bit quantised boxes, FP16 depth",
-            "batching": "binary BVH, FP32 depth, one CUDA-graph replay per step",
-            "perception": "binary BVH, FP32 depth, raw images block-averaged before the sensor, per-env camera "
-                          "pose/FOV randomisation, side masking (cols %s by mode)" % (tuple(w.rsm_cols),)}[variant]
+    form = BVH_NAMES[bvh] + ", " + {
+        "plain": "FP32 depth", "precision": "FP16 depth",
+        "batching": "FP32 depth, one CUDA-graph replay per step",
+        "perception": "FP32 depth, raw images block-averaged before the sensor, per-env camera pose/FOV "
+                      "randomisation, side masking (cols %s by mode)" % (tuple(w.rsm_cols),)}[variant]
     return ("%s: %d envs x cams (%s px); terrain %d tris (tiles of 8x8 m at 0.05 m: stairs 0.22/0.25/0.30 m run, "
             "20 deg slopes, stepping stones); %d links x %d-tri meshes; %s; %s"
             % (variant, w.n_envs, cams, len(w.terrain_tris), w.n_links, len(w.link_tris[0]), sensor, form))
@@ -103,13 +120,13 @@ def peaks():
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("render.cu", "render.h", "bvh.h"):
+    for f in ("render.cu", "render.h", "bvh.h", "bvh4.h", "bvh8.h"):
         with open(os.path.join(ROOT, "paper_2602_03002_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(rays, variant, tuning):
+def traffic_per_launch(rays, variant, tuning, bvh):
     """DRAM bytes per launch from the committed ncu capture, scaled by rays; None if the kernel, the
     variant or the launch shape differ from what was captured."""
     try:
@@ -119,7 +136,8 @@ def traffic_per_launch(rays, variant, tuning):
         return None
     sha = kernel_hash()
     for t in entries:
-        if t.get("kernel_sha") == sha and t.get("variant") == variant and t.get("tuning") == tuning:
+        if (t.get("kernel_sha") == sha and t.get("variant") == variant and t.get("tuning") == tuning
+                and t.get("bvh", 2) == bvh):
             return float(t["dram_bytes"]) * rays / float(t["rays"])
     return None
 
@@ -232,7 +250,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": rate / 1e9, "unit": "Grays/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt_tot / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_name(w, args.variant)},
+            "data": "synthetic", "config": {"workload": workload_name(w, args.variant, bvh_number(args))},
             "frames_per_s": rate / (w.raw_pixels_per_env / len(w.cameras)),
             "e2e": {"value": rate / 1e9, "unit": "Grays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "cpu_baseline": {"value": rate / 1e9, "unit": "Grays/s", "cores": cores, "kind": "oracle",
@@ -255,7 +273,7 @@ def run_ours(args):
         torch.distributed.barrier()
     w = workload(args, rank)
     env_offset = rank * args.envs
-    kind = rpl.RPL_BVH8Q8 if args.variant == "precision" else rpl.RPL_BVH2
+    kind = bvh_kind(args, rpl)
     t0 = time.perf_counter()
     scene = rpl.Scene(w.terrain_verts, w.terrain_tris, device=dev, bvh_kind=kind)
     for l, (v_, t_) in enumerate(zip(w.link_verts, w.link_tris)):
@@ -283,7 +301,7 @@ def run_ours(args):
         cnt = view.render_counters(poses[0], 0, env_offset, out, stream)
     stream.synchronize()
     gpu_step0 = out.float().cpu().numpy() if out.dtype != torch.uint16 else out.cpu().numpy().astype(np.float32)
-    node_bytes = 80 if kind == rpl.RPL_BVH8Q8 else 64
+    node_bytes = {rpl.RPL_BVH2: 64, rpl.RPL_BVH8Q8: 80, rpl.RPL_BVH4: 128}[kind]
     b_nodes = cnt["terrain_nodes"] * node_bytes + cnt["link_nodes"] * 64
     b_tris = (cnt["terrain_tris"] + cnt["link_tris"]) * TRI_BYTES
     b_boxes = cnt["link_boxes"] * BOX_BYTES
@@ -375,7 +393,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {0: "f32", 1: "f32 (f16 output)", 2: "f32 (unorm16 output)"}[w.sensor.out_dtype],
         "data": "synthetic", "variant": args.variant,
-        "config": {"workload": workload_name(w, args.variant), "envs_per_gpu": w.n_envs, "cameras": len(w.cameras),
+        "config": {"workload": workload_name(w, args.variant, bvh_number(args)), "envs_per_gpu": w.n_envs,
+                   "cameras": len(w.cameras), "bvh": BVH_NAMES[bvh_number(args)],
                    "rays_per_step_per_gpu": rays, "pose_sets": S, "tuning": tuning,
                    "autotune_best_ms": tune_ms,
                    "l2": "inputs larger than L2: terrain BVH %.2f GB resident, new poses each step"
@@ -384,7 +403,7 @@ def run_ours(args):
         "env_steps_per_s": world * w.n_envs / (ms_step / 1e3),
         "gpu_launches": ((3 if graph else 2) + (1 if raw_rays else 0)) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_per_launch(rays, args.variant, tuning),
+                     "frac": achieved / peak, "traffic": traffic_per_launch(rays, args.variant, tuning, bvh_number(args)),
                      "kernel": "render_kernel", "kernel_ms": 1e3 * k_avg_s,
                      "kernel_ms_source": "CUDA events around each render launch" if kms else
                                          "whole graph replay (events cannot be recorded inside the graph)",

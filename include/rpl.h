@@ -59,8 +59,10 @@ typedef struct rpl_view *rpl_view_t;     /* cameras, env count, sensor, per-env 
 /* Terrain acceleration structure.  RPL_BVH2: binary BVH with FP32 child boxes (64-byte nodes).
  * RPL_BVH8Q8: eight-wide BVH whose child boxes are quantised to 8 bits per bound on a per-node
  * power-of-two grid and rounded outward (80-byte nodes); traversal and triangle tests stay FP32,
- * so the depth is the same, only the culling is coarser.  Link meshes always use RPL_BVH2. */
-typedef enum { RPL_BVH2 = 0, RPL_BVH8Q8 = 1 } rpl_bvh_kind;
+ * so the depth is the same, only the culling is coarser.  RPL_BVH4: the binary tree collapsed to
+ * four children per node with FP32 boxes (128-byte nodes, half the depth, the same triangles);
+ * exact like RPL_BVH2.  Link meshes always use RPL_BVH2. */
+typedef enum { RPL_BVH2 = 0, RPL_BVH8Q8 = 1, RPL_BVH4 = 2 } rpl_bvh_kind;
 typedef enum { RPL_DEPTH_Z = 0, RPL_DEPTH_RANGE = 1 } rpl_depth_kind;
 /* Output element type.  F32: float.  F16: IEEE half, round to nearest (max error 1/2 ulp of half:
  * 0.98 mm in [2, 4) m).  U16: unsigned normalised over [0, d_max], q = rint(z / d_max * 65535)

@@ -18,8 +18,8 @@ LIB = os.path.join(HERE, "librpl.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["render.cu", "rpl_api.cpp", "bvh_build.cpp", "bvh8.cpp", "noalloc.cu", "server.cpp"]
-HEADERS = ["bvh.h", "bvh8.h", "render.h", "scene_access.h"]
+SOURCES = ["render.cu", "rpl_api.cpp", "bvh_build.cpp", "bvh8.cpp", "bvh4.cpp", "noalloc.cu", "server.cpp"]
+HEADERS = ["bvh.h", "bvh8.h", "bvh4.h", "render.h", "scene_access.h"]
 
 
 def _nvcc() -> str:

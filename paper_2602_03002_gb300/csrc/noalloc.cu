@@ -143,7 +143,7 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
         pp.poses = link_poses;
         pp.link_root = si.link_root;
         pp.tnodes = si.tnodes;
-        pp.wide = si.wide;
+        pp.bvh_kind = si.bvh_kind;
         pp.intr = nullptr;
         pp.link_xf = reinterpret_cast<float4 *>(sb);
         pp.link_box = reinterpret_cast<float4 *>(sb + off_box);
@@ -158,7 +158,7 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
             RenderParams rp{};
             rp.tnodes = si.tnodes;
             rp.ttris = si.ttris;
-            rp.wide = si.wide;
+            rp.bvh_kind = si.bvh_kind;
             rp.out_dtype = RPL_OUT_F32;
             rp.lnodes = si.lnodes;
             rp.ltris = si.ltris;

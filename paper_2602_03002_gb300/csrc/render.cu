@@ -116,6 +116,15 @@ __device__ __forceinline__ int descend_binary(const float4 *__restrict__ nodes, 
 // The same for the eight-wide layout (defined with the wide traversal below).
 __device__ __forceinline__ int descend_wide(const float4 *__restrict__ nodes, int node, const float lo[3],
                                             const float hi[3]);
+__device__ __forceinline__ int descend4(const float4 *__restrict__ nodes, int node, const float lo[3], const float hi[3]);
+
+// Entry node of the terrain walk for the layout `kind` (rpl_bvh_kind).
+__device__ __forceinline__ int descend_any(int kind, const float4 *__restrict__ nodes, int node, const float lo[3],
+                                           const float hi[3]) {
+    if (kind == RPL_BVH8Q8) return descend_wide(nodes, node, lo, hi);
+    if (kind == RPL_BVH4) return descend4(nodes, node, lo, hi);
+    return descend_binary(nodes, node, lo, hi);
+}
 
 __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepParams p) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -243,7 +252,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
 
     // 2) terrain entry node: descend while exactly one child's box meets the view volume's AABB and
     //    that child is an inner node; nothing in the other subtrees can be hit by this camera's rays
-    const int node = p.wide ? descend_wide(p.tnodes, 0, flo, fhi) : descend_binary(p.tnodes, 0, flo, fhi);
+    const int node = descend_any(p.bvh_kind, p.tnodes, 0, flo, fhi);
     // 3) latency of this (env, camera, step): k = (w0 (Lmax + 1)) >> 32 from the word with pixel field
     //    0xFFFFFFFF; source step s' = max(s - k, first step since reset); stored as s - s'
     uint32_t delta = 0;
@@ -437,6 +446,115 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
         while (pending < 0) {
             const int ref = ~pending;
             leaf<kSplit, kCount>(tris, ref >> 3, (ref & 7) + 1, r, tmax, hit, cnt);
+            pending = 0;
+            if (cur < 0 && cur != kDone) {
+                pending = cur;
+                cur = pop();
+            }
+        }
+        if (cur == kDone) return ok;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Four-wide BVH with FP32 boxes (layout in bvh4.h)
+// ---------------------------------------------------------------------------------------------
+struct Node4 {
+    float4 lx, hx, ly, hy, lz, hz;
+    int4 ch, cn;
+};
+
+__device__ __forceinline__ Node4 load4(const float4 *__restrict__ nodes, int i) {
+    const float4 *n = nodes + 8 * (int64_t)i;
+    return Node4{__ldg(n), __ldg(n + 1), __ldg(n + 2), __ldg(n + 3), __ldg(n + 4), __ldg(n + 5),
+                 __ldg(reinterpret_cast<const int4 *>(n + 6)), __ldg(reinterpret_cast<const int4 *>(n + 7))};
+}
+
+// Deepest four-wide node below `node` that holds everything inside the AABB [lo, hi]: descend while
+// exactly one child box meets the AABB and that child is an inner node (unused slots sit at 1e30).
+__device__ __forceinline__ int descend4(const float4 *__restrict__ nodes, int node, const float lo[3], const float hi[3]) {
+#pragma unroll 1
+    for (int depth = 0; depth < kStackDepth; ++depth) {
+        const Node4 n = load4(nodes, node);
+        const bool o0 = boxes_overlap(n.lx.x, n.hx.x, n.ly.x, n.hy.x, n.lz.x, n.hz.x, lo, hi);
+        const bool o1 = boxes_overlap(n.lx.y, n.hx.y, n.ly.y, n.hy.y, n.lz.y, n.hz.y, lo, hi);
+        const bool o2 = boxes_overlap(n.lx.z, n.hx.z, n.ly.z, n.hy.z, n.lz.z, n.hz.z, lo, hi);
+        const bool o3 = boxes_overlap(n.lx.w, n.hx.w, n.ly.w, n.hy.w, n.lz.w, n.hz.w, lo, hi);
+        if ((int)o0 + (int)o1 + (int)o2 + (int)o3 != 1) break;
+        const int c = o0 ? n.ch.x : (o1 ? n.ch.y : (o2 ? n.ch.z : n.ch.w));
+        if (c < 0) break;
+        node = c;
+    }
+    return node;
+}
+
+// Compare-exchange of (distance, reference) pairs, ascending by distance.
+__device__ __forceinline__ void cmp_swap(float &ta, int &ea, float &tb, int &eb) {
+    const bool sw = tb < ta;
+    const float t = sw ? tb : ta;
+    const int e = sw ? eb : ea;
+    tb = sw ? ta : tb;
+    eb = sw ? ea : eb;
+    ta = t;
+    ea = e;
+}
+
+// Closest hit in the four-wide terrain BVH, with the same two-phase leaf handling as the binary
+// traversal: the four child boxes of a node are tested from one 128-byte fetch, the hit children
+// are sorted by entry distance, the nearest is visited next and the others pushed far to near.
+template <bool kCount>
+__device__ __forceinline__ bool traverse4(const float4 *__restrict__ nodes, const float4 *__restrict__ tris, int root,
+                                          const Ray &r, float &tmax, bool &hit, Counts &cnt) {
+    int stack_node[kStackDepth];
+    int sp = 0;
+    bool ok = true;
+    int cur = root;
+    int pending = 0;
+    auto pop = [&]() -> int { return stack_pop(stack_node, sp); };
+#pragma unroll 1
+    for (;;) {
+#pragma unroll 1
+        while (cur >= 0) {
+            const Node4 n = load4(nodes, cur);
+            if (kCount) ++cnt.nodes;
+            float t0 = slab(r, n.lx.x, n.hx.x, n.ly.x, n.hy.x, n.lz.x, n.hz.x, tmax);
+            float t1 = slab(r, n.lx.y, n.hx.y, n.ly.y, n.hy.y, n.lz.y, n.hz.y, tmax);
+            float t2 = slab(r, n.lx.z, n.hx.z, n.ly.z, n.hy.z, n.lz.z, n.hz.z, tmax);
+            float t3 = slab(r, n.lx.w, n.hx.w, n.ly.w, n.hy.w, n.lz.w, n.hz.w, tmax);
+            int e0 = n.ch.x >= 0 ? n.ch.x : leaf_ref(n.ch.x, n.cn.x);
+            int e1 = n.ch.y >= 0 ? n.ch.y : leaf_ref(n.ch.y, n.cn.y);
+            int e2 = n.ch.z >= 0 ? n.ch.z : leaf_ref(n.ch.z, n.cn.z);
+            int e3 = n.ch.w >= 0 ? n.ch.w : leaf_ref(n.ch.w, n.cn.w);
+            cmp_swap(t0, e0, t1, e1);
+            cmp_swap(t2, e2, t3, e3);
+            cmp_swap(t0, e0, t2, e2);
+            cmp_swap(t1, e1, t3, e3);
+            cmp_swap(t1, e1, t2, e2);
+            const int nh = (int)(t0 != CUDART_INF_F) + (int)(t1 != CUDART_INF_F) + (int)(t2 != CUDART_INF_F) +
+                           (int)(t3 != CUDART_INF_F);
+            if (nh == 0) {
+                cur = pop();
+            } else {
+                if (sp + nh - 1 > kStackDepth) {
+                    ok = false;
+                    cur = kDone;
+                    break;
+                }
+                if (nh > 3) stack_node[sp++] = e3;
+                if (nh > 2) stack_node[sp++] = e2;
+                if (nh > 1) stack_node[sp++] = e1;
+                cur = e0;
+            }
+            if (cur < 0 && cur != kDone && pending == 0) {
+                pending = cur;
+                cur = pop();
+            }
+            if (!__any_sync(__activemask(), pending == 0 && cur >= 0)) break;
+        }
+#pragma unroll 1
+        while (pending < 0) {
+            const int ref = ~pending;
+            leaf<true, kCount>(tris, ref >> 3, (ref & 7) + 1, r, tmax, hit, cnt);
             pending = 0;
             if (cur < 0 && cur != kDone) {
                 pending = cur;
@@ -660,7 +778,7 @@ __device__ __forceinline__ void finish_pixel(const RenderParams &p, int e, int c
     }
 }
 
-template <bool kCount, bool kWide>
+template <bool kCount, int kKind>
 __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp, int lane, int64_t step) {
     const int e = (int)(warp / p.tiles_per_env);
     const int r_tile = (int)(warp - (int64_t)e * p.tiles_per_env);
@@ -723,8 +841,7 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
             thi[a] = hi + slack;
         }
     }
-    const int entry = kWide ? descend_wide(p.tnodes, __float_as_int(CV.z), tlo, thi)
-                             : descend_binary(p.tnodes, __float_as_int(CV.z), tlo, thi);
+    const int entry = descend_any(kKind, p.tnodes, __float_as_int(CV.z), tlo, thi);
     uint64_t link_mask = 0;
 #pragma unroll 1
     for (uint64_t mk = cam_mask; mk; mk &= mk - 1) {
@@ -764,9 +881,11 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
     };
     // 2) static terrain, bounded by the closest hit so far
     auto query_terrain = [&]() {
-        if (kWide) {
+        if (kKind == RPL_BVH8Q8) {
             const int oct = (d.x < 0.f ? 1 : 0) | (d.y < 0.f ? 2 : 0) | (d.z < 0.f ? 4 : 0);
             ok &= traverse8<kCount>(p.tnodes, p.ttris, entry, ray, oct, tmax, hit, cnt_t);
+        } else if (kKind == RPL_BVH4) {
+            ok &= traverse4<kCount>(p.tnodes, p.ttris, entry, ray, tmax, hit, cnt_t);
         } else {
             ok &= traverse<true, kCount>(p.tnodes, p.ttris, entry, ray, tmax, hit, cnt_t);
         }
@@ -802,7 +921,7 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
 // kMinBlocks caps registers so that many blocks of 128 threads stay resident per SM (8 -> 64
 // registers, 10 -> 48, 12 -> 40).  With p.persistent the grid holds only as many blocks as fit on
 // the device at once and each warp walks the tiles with a grid stride; otherwise one warp per tile.
-template <bool kCount, bool kWide, int kMinBlocks>
+template <bool kCount, int kKind, int kMinBlocks>
 __global__ void __launch_bounds__(128, kMinBlocks) render_kernel(const __grid_constant__ RenderParams p) {
     const int lane = threadIdx.x & 31;
     const int64_t total = (int64_t)p.E * p.tiles_per_env;
@@ -810,13 +929,13 @@ __global__ void __launch_bounds__(128, kMinBlocks) render_kernel(const __grid_co
     const int64_t step = p.step_dev ? *p.step_dev : p.step;
 #pragma unroll 1
     for (int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); warp < total; warp += stride)
-        render_tile<kCount, kWide>(p, warp, lane, step);
+        render_tile<kCount, kKind>(p, warp, lane, step);
 }
 
 // Several render requests (each with its own view, envs, cameras and sensor) in one launch: the
 // tiles of request r occupy warps [prefix[r], prefix[r + 1]); each warp finds its request by binary
 // search and renders one tile with that request's parameters (read from global memory).
-template <bool kWide, int kMinBlocks>
+template <int kKind, int kMinBlocks>
 __global__ void __launch_bounds__(128, kMinBlocks)
     render_multi_kernel(const RenderParams *__restrict__ reqs, const int64_t *__restrict__ prefix, int n_req) {
     const int lane = threadIdx.x & 31;
@@ -832,7 +951,7 @@ __global__ void __launch_bounds__(128, kMinBlocks)
         }
         const RenderParams &p = reqs[lo];
         const int64_t step = p.step_dev ? *p.step_dev : p.step;
-        render_tile<false, kWide>(p, warp - prefix[lo], lane, step);
+        render_tile<false, kKind>(p, warp - prefix[lo], lane, step);
         if (p.done_counter) {
             // per-request completion inside the fused launch: every lane's stores are made visible,
             // then the warp counts its tile off; the warp that finishes the request's last tile
@@ -889,6 +1008,34 @@ cudaError_t launch_prep(const PrepParams &p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+namespace {
+
+// The render kernel for one terrain layout; the counting variant runs with 8 blocks per SM.
+template <int kKind>
+void launch_kind(const RenderParams &p, bool count, int min_blocks, unsigned g, cudaStream_t s) {
+    if (count)
+        render_kernel<true, kKind, 8><<<g, 128, 0, s>>>(p);
+    else if (min_blocks == 12)
+        render_kernel<false, kKind, 12><<<g, 128, 0, s>>>(p);
+    else if (min_blocks == 10)
+        render_kernel<false, kKind, 10><<<g, 128, 0, s>>>(p);
+    else
+        render_kernel<false, kKind, 8><<<g, 128, 0, s>>>(p);
+}
+
+template <int kKind>
+void launch_multi_kind(const RenderParams *reqs_dev, const int64_t *prefix_dev, int n_req, int min_blocks, unsigned g,
+                       cudaStream_t s) {
+    if (min_blocks == 12)
+        render_multi_kernel<kKind, 12><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
+    else if (min_blocks == 10)
+        render_multi_kernel<kKind, 10><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
+    else
+        render_multi_kernel<kKind, 8><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
+}
+
+}  // namespace
+
 cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
     const int64_t warps = (int64_t)p.E * p.tiles_per_env;
     if (warps == 0) return cudaSuccess;
@@ -902,27 +1049,12 @@ cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
     }
     (void)cudaGetLastError();
     const unsigned g = (unsigned)blocks;
-    if (count) {
-        if (p.wide)
-            render_kernel<true, true, 8><<<g, 128, 0, s>>>(p);
-        else
-            render_kernel<true, false, 8><<<g, 128, 0, s>>>(p);
-    } else if (min_blocks == 12) {
-        if (p.wide)
-            render_kernel<false, true, 12><<<g, 128, 0, s>>>(p);
-        else
-            render_kernel<false, false, 12><<<g, 128, 0, s>>>(p);
-    } else if (min_blocks == 10) {
-        if (p.wide)
-            render_kernel<false, true, 10><<<g, 128, 0, s>>>(p);
-        else
-            render_kernel<false, false, 10><<<g, 128, 0, s>>>(p);
-    } else {
-        if (p.wide)
-            render_kernel<false, true, 8><<<g, 128, 0, s>>>(p);
-        else
-            render_kernel<false, false, 8><<<g, 128, 0, s>>>(p);
-    }
+    if (p.bvh_kind == RPL_BVH8Q8)
+        launch_kind<RPL_BVH8Q8>(p, count, min_blocks, g, s);
+    else if (p.bvh_kind == RPL_BVH4)
+        launch_kind<RPL_BVH4>(p, count, min_blocks, g, s);
+    else
+        launch_kind<RPL_BVH2>(p, count, min_blocks, g, s);
     return cudaGetLastError();
 }
 
@@ -940,7 +1072,7 @@ cudaError_t launch_downsample(const RenderParams &p, cudaStream_t s) {
 }
 
 cudaError_t launch_render_multi(const RenderParams *reqs_dev, const int64_t *prefix_dev, int n_req,
-                                int64_t total_warps, bool wide, int min_blocks, bool persistent, cudaStream_t s) {
+                                int64_t total_warps, int bvh_kind, int min_blocks, bool persistent, cudaStream_t s) {
     if (total_warps <= 0 || n_req <= 0) return cudaSuccess;
     int64_t blocks = (total_warps + 3) / 4;
     const int mb = min_blocks == 12 ? 12 : (min_blocks == 10 ? 10 : 8);
@@ -952,21 +1084,12 @@ cudaError_t launch_render_multi(const RenderParams *reqs_dev, const int64_t *pre
     }
     (void)cudaGetLastError();
     const unsigned g = (unsigned)blocks;
-    if (wide) {
-        if (mb == 12)
-            render_multi_kernel<true, 12><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
-        else if (mb == 10)
-            render_multi_kernel<true, 10><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
-        else
-            render_multi_kernel<true, 8><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
-    } else {
-        if (mb == 12)
-            render_multi_kernel<false, 12><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
-        else if (mb == 10)
-            render_multi_kernel<false, 10><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
-        else
-            render_multi_kernel<false, 8><<<g, 128, 0, s>>>(reqs_dev, prefix_dev, n_req);
-    }
+    if (bvh_kind == RPL_BVH8Q8)
+        launch_multi_kind<RPL_BVH8Q8>(reqs_dev, prefix_dev, n_req, mb, g, s);
+    else if (bvh_kind == RPL_BVH4)
+        launch_multi_kind<RPL_BVH4>(reqs_dev, prefix_dev, n_req, mb, g, s);
+    else
+        launch_multi_kind<RPL_BVH2>(reqs_dev, prefix_dev, n_req, mb, g, s);
     return cudaGetLastError();
 }
 

@@ -30,8 +30,8 @@ struct CamDev {
 struct PrepParams {
     const float *poses;        // [E, L, 7]
     const float4 *link_root;   // [RPL_MAX_LINKS * 2] link-frame root boxes (lo, hi)
-    const float4 *tnodes;      // terrain BVH nodes (binary layout, or wide layout when wide != 0)
-    int32_t wide;              // 1: terrain nodes are 80-byte eight-wide quantised nodes (bvh8.h)
+    const float4 *tnodes;      // terrain BVH nodes in the layout of bvh_kind
+    int32_t bvh_kind;          // rpl_bvh_kind: binary (bvh.h), eight-wide quantised (bvh8.h), four-wide (bvh4.h)
     const float *intr;         // [E, C, 4] per-env intrinsics or null
     const float *mount_dr;     // [E, C, 7] per-env mount perturbation (dp, dq xyzw) or null
     float4 *link_xf;
@@ -56,9 +56,9 @@ struct Tuning {
 };
 
 struct RenderParams {
-    const float4 *tnodes;   // terrain BVH nodes (4 float4 each, or 5 when wide), root = node 0
+    const float4 *tnodes;   // terrain BVH nodes (4, 5 or 8 float4 each by bvh_kind), root = node 0
     const float4 *ttris;    // terrain triangles (3 float4 each)
-    int32_t wide;           // 1: eight-wide quantised terrain BVH
+    int32_t bvh_kind;       // rpl_bvh_kind of the terrain BVH
     int32_t out_dtype;      // rpl_out_dtype of `out`
     const float4 *lnodes;   // all link BVH nodes
     const float4 *ltris;    // all link triangles
@@ -105,7 +105,7 @@ cudaError_t launch_advance_step(int64_t *step, cudaStream_t s);
 // One launch over several requests: reqs_dev[n_req] parameters in device memory, prefix_dev[n_req + 1]
 // the first warp of each request (prefix_dev[n_req] = total_warps).
 cudaError_t launch_render_multi(const RenderParams *reqs_dev, const int64_t *prefix_dev, int n_req,
-                                int64_t total_warps, bool wide, int min_blocks, bool persistent, cudaStream_t s);
+                                int64_t total_warps, int bvh_kind, int min_blocks, bool persistent, cudaStream_t s);
 
 // Depth of the traversal stack; scenes whose BVH is deeper are refused at build time.
 constexpr int kStackDepth = 64;

@@ -15,6 +15,7 @@
 
 #include "../../include/rpl.h"
 #include "bvh.h"
+#include "bvh4.h"
 #include "bvh8.h"
 #include "render.h"
 #include "scene_access.h"
@@ -207,7 +208,7 @@ RPL_API rpl_status rpl_scene_create(const float *verts, int64_t n_verts, const i
     if (n_tris >= (int64_t)0x0FFFFFFF) return fail(RPL_ERR_CAPACITY, "rpl_scene_create: too many triangles");
     rpl_scene_opts o{};
     if (opts) o = *opts;
-    if (o.bvh_kind != RPL_BVH2 && o.bvh_kind != RPL_BVH8Q8)
+    if (o.bvh_kind != RPL_BVH2 && o.bvh_kind != RPL_BVH8Q8 && o.bvh_kind != RPL_BVH4)
         return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: unknown bvh_kind %d", o.bvh_kind);
     if (o.max_leaf_size < 0 || o.max_leaf_size > 8)
         return fail(RPL_ERR_INVALID_ARG, "rpl_scene_create: max_leaf_size must be 0..8");
@@ -255,8 +256,24 @@ RPL_API rpl_status rpl_scene_create(const float *verts, int64_t n_verts, const i
         size_t node_bytes = bvh.nodes.size() * sizeof(BvhNode);
         const std::vector<BvhTri> *tri_src = &bvh.tris;
         HostBvh8 wide;
+        HostBvh4 four;
         s->t_n_nodes = (int64_t)bvh.nodes.size();
         s->t_depth = bvh.depth;
+        if (o.bvh_kind == RPL_BVH4) {
+            collapse_bvh4(bvh, &four);
+            // a four-wide node pushes at most three children
+            if (3 * four.depth > kStackDepth) {
+                delete s;
+                return fail(RPL_ERR_CAPACITY, "rpl_scene_create: four-wide BVH depth %d exceeds %d", four.depth,
+                            kStackDepth / 3);
+            }
+            bvh.nodes.clear();
+            bvh.nodes.shrink_to_fit();
+            node_src = four.nodes.data();
+            node_bytes = four.nodes.size() * sizeof(Bvh4Node);
+            s->t_n_nodes = (int64_t)four.nodes.size();
+            s->t_depth = four.depth;
+        }
         if (o.bvh_kind == RPL_BVH8Q8) {
             if (collapse_bvh8(bvh, &wide) != 0) {
                 delete s;
@@ -369,7 +386,8 @@ RPL_API rpl_status rpl_scene_info_get(rpl_scene_t s, rpl_scene_info *info) {
     std::lock_guard<std::mutex> lk(s->mu);
     info->terrain_tris = s->t_n_tris;
     info->terrain_nodes = s->t_n_nodes;
-    info->terrain_bytes = s->t_n_nodes * (int64_t)(s->opts.bvh_kind == RPL_BVH8Q8 ? sizeof(Bvh8Node) : sizeof(BvhNode)) +
+    info->terrain_bytes = s->t_n_nodes * (int64_t)(s->opts.bvh_kind == RPL_BVH8Q8 ? sizeof(Bvh8Node)
+                                                   : s->opts.bvh_kind == RPL_BVH4 ? sizeof(Bvh4Node) : sizeof(BvhNode)) +
                           s->t_n_tris * (int64_t)sizeof(BvhTri);
     info->terrain_depth = s->t_depth;
     int n = 0;
@@ -730,7 +748,7 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
     pp.poses = poses_dev;
     pp.link_root = s->l_roots.as<const float4>();
     pp.tnodes = s->t_nodes.as<const float4>();
-    pp.wide = s->opts.bvh_kind == RPL_BVH8Q8 ? 1 : 0;
+    pp.bvh_kind = s->opts.bvh_kind;
     pp.intr = v->intr.p ? v->intr.as<const float>() : nullptr;
     pp.mount_dr = v->mount_dr.p ? v->mount_dr.as<const float>() : nullptr;
     for (int l = 0; l < RPL_MAX_LINKS; ++l) pp.lroot[l] = l < v->L ? s->l_root[l] : -1;
@@ -752,7 +770,7 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
     rp = RenderParams{};
     rp.tnodes = s->t_nodes.as<const float4>();
     rp.ttris = s->t_tris.as<const float4>();
-    rp.wide = pp.wide;
+    rp.bvh_kind = pp.bvh_kind;
     rp.out_dtype = v->sensor.out_dtype;
     rp.lnodes = s->l_nodes.as<const float4>();
     rp.ltris = s->l_tris.as<const float4>();
@@ -1278,7 +1296,7 @@ bool scene_inputs(const rpl_scene *s, SceneInputs *out) {
     std::lock_guard<std::mutex> lk(const_cast<rpl_scene *>(s)->mu);
     if (!s->frozen) return false;
     out->device = s->device;
-    out->wide = s->opts.bvh_kind == RPL_BVH8Q8 ? 1 : 0;
+    out->bvh_kind = s->opts.bvh_kind;
     out->tnodes = s->t_nodes.as<const float4>();
     out->ttris = s->t_tris.as<const float4>();
     out->lnodes = s->l_nodes.as<const float4>();
@@ -1323,7 +1341,7 @@ int32_t view_envs(const rpl_view *v) { return v->E; }
 rpl_scene *view_scene(const rpl_view *v) { return v->scene; }
 Tuning view_tuning(const rpl_view *v) { return v->tune; }
 int scene_device_of(const rpl_scene *s) { return s->device; }
-bool scene_is_wide(const rpl_scene *s) { return s->opts.bvh_kind == RPL_BVH8Q8; }
+int scene_bvh_kind(const rpl_scene *s) { return s->opts.bvh_kind; }
 bool pointer_on_device(const void *p, int device) { return pointer_kind(p, device) == PTR_DEVICE; }
 
 void scene_add_server(rpl_scene *s) {

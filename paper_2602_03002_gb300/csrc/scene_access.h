@@ -10,7 +10,7 @@ namespace rpl {
 
 struct SceneInputs {
     int device;
-    int wide;   // 1: the terrain BVH uses the eight-wide quantised layout
+    int bvh_kind;   // rpl_bvh_kind of the terrain BVH
     const float4 *tnodes, *ttris, *lnodes, *ltris, *link_root;
     int32_t lroot[RPL_MAX_LINKS];
 };
@@ -38,7 +38,7 @@ int32_t view_envs(const rpl_view *v);
 rpl_scene *view_scene(const rpl_view *v);
 Tuning view_tuning(const rpl_view *v);
 int scene_device_of(const rpl_scene *s);
-bool scene_is_wide(const rpl_scene *s);
+int scene_bvh_kind(const rpl_scene *s);
 bool pointer_on_device(const void *p, int device);
 // A server keeps its scene alive: rpl_scene_destroy is deferred until the last server (and view) goes.
 void scene_add_server(rpl_scene *s);

@@ -123,7 +123,7 @@ struct Slot {
 struct rpl_server {
     rpl_scene *scene = nullptr;
     int device = 0;
-    bool wide = false;
+    int bvh_kind = RPL_BVH2;
     rpl_server_opts opts{};
     unsigned char *arena_dev = nullptr;
     Arena arena;
@@ -201,7 +201,7 @@ void launch_batch(rpl_server *sv, Slot &s) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s.d_remaining, s.h_remaining, (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = launch_render_multi(s.d_params, s.d_prefix, n, total, sv->wide, sv->opts.min_blocks,
+        e = launch_render_multi(s.d_params, s.d_prefix, n, total, sv->bvh_kind, sv->opts.min_blocks,
                                 sv->opts.persistent != 0, st);
     for (int i = 0; i < n && e == cudaSuccess; ++i)   // downsampled cameras of a request: average + sensor
         if (s.reqs[i]->status == RPL_OK && s.h_params[i].raw_per_env > 0) e = launch_downsample(s.h_params[i], st);
@@ -385,7 +385,7 @@ RPL_API rpl_status rpl_server_create(rpl_scene_t scene, const rpl_server_opts *o
     if (!sv) return server_fail(RPL_ERR_OUT_OF_MEMORY, "rpl_server_create: host allocation");
     sv->scene = scene;
     sv->device = si.device;
-    sv->wide = si.wide != 0;
+    sv->bvh_kind = si.bvh_kind;
     sv->opts = o;
     cudaError_t e = cudaMalloc(&sv->arena_dev, std::max<size_t>((size_t)o.staging_bytes, kAlign));
     sv->arena.reset((size_t)o.staging_bytes);

@@ -23,7 +23,7 @@ _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "NOT_FOU
 RPL_MAX_CAMERAS = 8
 RPL_MAX_LINKS = 64
 RPL_DEPTH_Z, RPL_DEPTH_RANGE = 0, 1
-RPL_BVH2, RPL_BVH8Q8 = 0, 1
+RPL_BVH2, RPL_BVH8Q8, RPL_BVH4 = 0, 1, 2
 RPL_OUT_F32, RPL_OUT_F16, RPL_OUT_U16 = 0, 1, 2
 
 
