@@ -249,6 +249,13 @@ RPL_API rpl_status rpl_view_layout(rpl_view_t view, int64_t *cam_offsets, int64_
 RPL_API rpl_status rpl_render(rpl_view_t view, const float *link_poses, int64_t step,
                               int64_t env_offset, void *depth_out, void *stream);
 
+/* Asynchronous host output.  When enabled, rpl_render with a host depth_out returns after
+ * enqueuing: the depth is staged in one of two view-owned device buffers (used in turn) and copied
+ * to depth_out on a view-owned stream, overlapped with the next render; depth_out holds the result
+ * after rpl_sync (which waits for the copy), and must be pinned memory for the copy to overlap.
+ * Disabling waits for the view's work.  Errors: INVALID_ARG, CUDA. */
+RPL_API rpl_status rpl_view_host_async(rpl_view_t view, int32_t enable);
+
 /* Launch shape of the render kernel.  tile_w x tile_h = 32 rays per warp (4x8, 8x4 or 16x2
  * pixels of one camera); persistent: launch only as many blocks as fit on the GPU at once and let
  * warps stride over the tiles; terrain_first: query the terrain before the links (Alg. 1 queries

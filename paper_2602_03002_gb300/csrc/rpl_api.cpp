@@ -156,6 +156,13 @@ struct rpl_view {
     bool cams_set = false;
     rpl_sensor_params sensor{};
     DevBuf link_xf, link_box, cam_xf, intr, ring, s_first, mask_stage, pose_stage, out_stage;
+    // asynchronous host output (rpl_view_host_async): a second staging buffer, the copy stream and
+    // per-buffer events (render finished writing / copy finished reading)
+    bool host_async = false;
+    DevBuf out_stage2;
+    int stage_next = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t rendered[2] = {}, copied[2] = {};
     // downsampled cameras: raw depths [E, raw_per_env]; camera c's raw image starts at raw_off[c]
     DevBuf raw;
     int64_t raw_per_env = 0;
@@ -897,18 +904,33 @@ RPL_API rpl_status rpl_render(rpl_view_t v, const float *poses, int64_t step, in
         if (e != cudaSuccess) return cuda_fail(e, "rpl_render: copying poses to the device");
         pd = v->pose_stage.as<const float>();
     }
+    const bool async_out = ok == PTR_HOST && v->host_async;
+    const int k = v->stage_next;
     if (ok == PTR_HOST) {
-        if (v->out_stage.bytes < out_bytes) {
-            e = v->out_stage.alloc(out_bytes);
+        DevBuf &stage = async_out && k == 1 ? v->out_stage2 : v->out_stage;
+        if (stage.bytes < out_bytes) {
+            if (async_out) cudaEventSynchronize(v->copied[k]);   // the buffer may still be copied from
+            e = stage.alloc(out_bytes);
             if (e != cudaSuccess) return cuda_fail(e, "rpl_render: allocating the output staging buffer");
         }
-        od = v->out_stage.p;
+        od = stage.p;
+        // the render may overwrite this staging buffer only after its previous copy to the host
+        if (async_out) cudaStreamWaitEvent(cs, v->copied[k], 0);
     }
     st = enqueue(v, pd, step, env_offset, od, cs, false, nullptr);
     if (st != RPL_OK) return st;
     v->has_last = true;
     v->last_step = step;
-    if (ok == PTR_HOST) {
+    if (async_out) {
+        // the copy to the host runs on the view's copy stream, overlapped with the next render
+        e = cudaEventRecord(v->rendered[k], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(v->copy_stream, v->rendered[k], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, od, out_bytes, cudaMemcpyDeviceToHost, v->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(v->copied[k], v->copy_stream);
+        if (e != cudaSuccess) return cuda_fail(e, "rpl_render: enqueuing the copy of depth to the host");
+        mark_done(v, v->copy_stream);   // rpl_sync waits for the copy (which waited for the render)
+        v->stage_next = 1 - k;
+    } else if (ok == PTR_HOST) {
         e = cudaMemcpyAsync(out, od, out_bytes, cudaMemcpyDeviceToHost, cs);
         if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
         if (e != cudaSuccess) return cuda_fail(e, "rpl_render: copying depth to the host");
@@ -1066,6 +1088,22 @@ RPL_API rpl_status rpl_sync(rpl_view_t v) {
         *v->err_host = 0;
         return fail(RPL_ERR_DEVICE_FAULT, "rpl_sync: a render kernel recorded error 0x%x (traversal stack overflow)", w);
     }
+    return RPL_OK;
+}
+
+RPL_API rpl_status rpl_view_host_async(rpl_view_t v, int32_t enable) {
+    if (!v) return fail(RPL_ERR_INVALID_ARG, "rpl_view_host_async: view is NULL");
+    DeviceGuard g(v->scene->device);
+    if (enable && !v->copy_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&v->copy_stream, cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            e = cudaEventCreateWithFlags(&v->rendered[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->copied[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "rpl_view_host_async: creating the copy stream");
+    }
+    if (!enable && v->host_async && v->has_done) cudaEventSynchronize(v->done);
+    v->host_async = enable != 0;
     return RPL_OK;
 }
 
@@ -1281,6 +1319,11 @@ RPL_API void rpl_view_destroy(rpl_view_t v) {
             if (v->ev[i]) cudaEventDestroy(v->ev[i]);
         graph_release(v);
         if (v->cap_stream) cudaStreamDestroy(v->cap_stream);
+        for (int k = 0; k < 2; ++k) {
+            if (v->rendered[k]) cudaEventDestroy(v->rendered[k]);
+            if (v->copied[k]) cudaEventDestroy(v->copied[k]);
+        }
+        if (v->copy_stream) cudaStreamDestroy(v->copy_stream);
     }
     rpl_scene *s = v->scene;
     delete v;

@@ -280,3 +280,30 @@ def test_max_cameras_and_links(cuda, rpl_lib):
     compare_depth(outs[0], ref["depth"], ref["flags"], "max sizes")
     with pytest.raises(rpl_lib.RplError):
         rpl_lib.View(rpl_lib.Scene.from_workload(W.config_small(n_steps=1)), 2, n_links + 1)
+
+
+def test_async_host_output_equals_synchronous(cuda, rpl_lib):
+    """With rpl_view_host_async the host copies run on the view's copy stream from two staging
+    buffers in turn; after rpl_sync every step's host frame equals the synchronous result."""
+    torch = cuda
+    w = W.config_small(n_steps=6, n_envs=5)
+    sen = W.Sensor(sigma_abs=0.01, p_drop=0.05, max_latency=2, seed=(0xA5, 0x5A))
+    scene = rpl_lib.Scene.from_workload(w)
+    a = rpl_lib.View.from_workload(scene, w)
+    a.set_sensor(sen)
+    b = rpl_lib.View.from_workload(scene, w)
+    b.set_sensor(sen)
+    rpl_lib.rpl_view_host_async(b.h, True)
+    poses = [torch.from_numpy(w.poses[s]).pin_memory() for s in range(6)]
+    P = b.layout()[1]
+    ref = [a.render(poses[s], s).cpu().clone() for s in range(6)]     # synchronous host path
+    outs = [torch.empty((w.n_envs, P), dtype=torch.float32).pin_memory() for _ in range(6)]
+    for s in range(6):
+        rpl_lib.rpl_render(b.h, poses[s], s, 0, outs[s], None)
+    b.sync()
+    for s in range(6):
+        assert torch.equal(outs[s], ref[s]), s
+    rpl_lib.rpl_view_host_async(b.h, False)
+    again = torch.empty((w.n_envs, P), dtype=torch.float32).pin_memory()
+    rpl_lib.rpl_render(b.h, poses[5], 5, 0, again, None)          # synchronous again: re-render step 5
+    assert torch.equal(again, ref[5])
