@@ -340,7 +340,8 @@ RPL_API rpl_status rpl_server_submit(rpl_server_t server, rpl_view_t view, const
 /* Wait up to timeout_ms (< 0: forever) for a request; on completion returns its status, sets
  * *latency_s (submit to completion, host clock; may be NULL) and forgets the ticket.  Returns
  * RPL_ERR_TIMEOUT when it is still pending (the ticket stays valid), INVALID_ARG for an unknown
- * ticket. */
+ * ticket, for a ticket another thread is already waiting on, or when another thread cancels the
+ * request during the wait. */
 RPL_API rpl_status rpl_server_wait(rpl_server_t server, uint64_t ticket, int32_t timeout_ms, double *latency_s);
 
 /* Give up on a request: it still renders (so the view's step sequence stays whole) and is forgotten

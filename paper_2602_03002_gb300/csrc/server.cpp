@@ -101,6 +101,7 @@ struct Request {
     std::string err;
     bool done = false, cancelled = false;
     bool early = false;   // completes by its own flag inside the fused launch
+    bool waiting = false; // a thread is blocked in rpl_server_wait on it (it then owns the deletion)
 };
 
 struct Slot {
@@ -242,7 +243,7 @@ void finish(rpl_server *sv, Request *r, Clock::time_point now) {
         sv->stats.completed++;
     else
         sv->stats.failed++;
-    if (r->cancelled) {
+    if (r->cancelled && !r->waiting) {   // a waiter, woken by cv_done, deletes it instead
         sv->tickets.erase(r->id);
         delete r;
     }
@@ -482,15 +483,28 @@ RPL_API rpl_status rpl_server_wait(rpl_server_t sv, uint64_t ticket, int32_t tim
     if (it == sv->tickets.end() || it->second->cancelled)
         return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_wait: unknown ticket");
     Request *r = it->second;
+    if (r->waiting) return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_wait: another thread waits on this ticket");
+    r->waiting = true;
     auto pred = [&] { return r->done; };
+    bool done = true;
     if (timeout_ms < 0)
         sv->cv_done.wait(lk, pred);
-    else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
-        return server_fail(RPL_ERR_TIMEOUT, "rpl_server_wait: the request is still pending");
+    else
+        done = sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred);
+    r->waiting = false;
+    if (r->cancelled) {
+        // cancelled by another thread while this one waited: forget it once it has rendered
+        if (r->done) {
+            sv->tickets.erase(r->id);
+            delete r;
+        }
+        return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_wait: the request was cancelled");
+    }
+    if (!done) return server_fail(RPL_ERR_TIMEOUT, "rpl_server_wait: the request is still pending");
     const rpl_status st = r->status;
     const std::string err = r->err;
     if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
-    sv->tickets.erase(it);
+    sv->tickets.erase(r->id);
     delete r;
     if (st != RPL_OK) return server_fail(st, err);
     return RPL_OK;

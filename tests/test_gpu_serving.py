@@ -189,7 +189,7 @@ def test_small_request_fused_with_a_large_one_completes_first(cuda, rpl_lib):
     w = _workload()
     scene = rpl_lib.Scene.from_workload(w)
     big_w = W.config_small(n_steps=1, n_envs=16384)
-    blocker = rpl_lib.View(scene, 4096, w.n_links)
+    blocker = rpl_lib.View(scene, 16384, w.n_links)
     blocker.set_cameras(w.cameras)
     vb = rpl_lib.View(scene, 16384, w.n_links)
     vb.set_cameras(w.cameras)
@@ -205,7 +205,11 @@ def test_small_request_fused_with_a_large_one_completes_first(cuda, rpl_lib):
     (vs2, _, _, _), = _views(rpl_lib, torch, w, scene, [(3, 2)])
     server = rpl_lib.Server(scene, max_batch=8, n_streams=1)
     ob, os_ = vb2.out_tensor(), vs2.out_tensor()
-    t0 = server.submit(blocker, pb[:4096], 0, blocker.out_tensor())   # occupies the only slot
+    t0 = server.submit(blocker, pb, 0, blocker.out_tensor())   # occupies the only slot
+    import time
+    deadline = time.time() + 5.0
+    while server.stats()["batches"] < 1 and time.time() < deadline:   # the blocker is on the GPU
+        time.sleep(0.0001)
     tb = server.submit(vb2, pb, 0, ob)
     ts = server.submit(vs2, ps[0], 0, os_, 9)
     lat_s = server.wait(ts)
@@ -216,3 +220,45 @@ def test_small_request_fused_with_a_large_one_completes_first(cuda, rpl_lib):
     assert torch.equal(ob, alone_big) and torch.equal(os_, alone_small)
     assert st["max_batch_seen"] >= 2, st          # the two were fused
     assert lat_s < lat_b, (lat_s, lat_b)
+
+
+def test_cancel_while_another_thread_waits(cuda, rpl_lib):
+    """A cancel from one thread while another waits on the same ticket ends that wait (with the
+    result or an error) without touching a freed request; a second concurrent waiter is refused."""
+    torch = cuda
+    w = _workload()
+    scene = rpl_lib.Scene.from_workload(w)
+    big_w = W.config_small(n_steps=1, n_envs=8192)
+    vb = rpl_lib.View(scene, 8192, w.n_links)
+    vb.set_cameras(w.cameras)
+    pb = torch.from_numpy(np.ascontiguousarray(big_w.poses[0])).cuda()
+    server = rpl_lib.Server(scene, max_batch=4, n_streams=1)
+    for rep in range(3):
+        tk = server.submit(vb, pb, rep, vb.out_tensor())
+        result = {}
+
+        def waiter():
+            try:
+                rpl_lib.rpl_server_wait(server.h, tk, -1)
+                result["status"] = 0
+            except rpl_lib.RplError as e:
+                result["status"] = e.status
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        import time
+        time.sleep(0.002)
+        try:   # refused while the other thread waits; TIMEOUT or done otherwise, depending on timing
+            rpl_lib.rpl_server_wait(server.h, tk, 0)
+        except rpl_lib.RplError as e:
+            assert e.status in (1, 6)
+        try:
+            rpl_lib.rpl_server_cancel(server.h, tk)
+        except rpl_lib.RplError as e:           # the request completed and was consumed first
+            assert e.status == 1
+        th.join(10)
+        assert not th.is_alive()
+        assert result["status"] in (0, 1)
+    st = server.stats()
+    server.close()
+    assert st["submitted"] == 3 and st["failed"] == 0
