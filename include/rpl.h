@@ -249,6 +249,17 @@ RPL_API rpl_status rpl_view_layout(rpl_view_t view, int64_t *cam_offsets, int64_
 RPL_API rpl_status rpl_render(rpl_view_t view, const float *link_poses, int64_t step,
                               int64_t env_offset, void *depth_out, void *stream);
 
+/* The sensor model alone (Appendix A.2; Sec. 3.2.4 side mask) on caller-provided pre-sensor depth:
+ * depth_in, device, [n_envs, total_per_env] float32 in the view's output layout (rpl_view_layout),
+ * is taken as the raw depth of `step` (what the ray cast would give: the closest hit's z-depth, or
+ * d_max for a miss) and goes through the same ring buffer, latency, noise, clip, dropout and side
+ * mask as rpl_render, with the same step rules, into depth_out (device, the view's output type).
+ * For depth from another renderer, and to test the sensor model without ray casting.  Views with
+ * downsampled cameras are refused.  Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA,
+ * DEVICE_FAULT. */
+RPL_API rpl_status rpl_sensor_apply(rpl_view_t view, const float *depth_in, int64_t step, int64_t env_offset,
+                                    void *depth_out, void *stream);
+
 /* Asynchronous host output.  When enabled, rpl_render with a host depth_out returns after
  * enqueuing: the depth is staged in one of two view-owned device buffers (used in turn) and copied
  * to depth_out on a view-owned stream, overlapped with the next render; depth_out holds the result

@@ -990,6 +990,33 @@ __global__ void __launch_bounds__(256) downsample_kernel(const __grid_constant__
     }
 }
 
+// The sensor model alone on caller-provided pre-sensor depth `src` ([E, pix_per_env], the output
+// layout): one thread per output pixel; the latency of (env, camera, step) is drawn here the way the
+// prep kernel draws it.
+__global__ void __launch_bounds__(256) sensor_kernel(const __grid_constant__ RenderParams p, const float *src) {
+    const int64_t total = (int64_t)p.E * p.pix_per_env;
+    const int64_t step = p.step;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i / p.pix_per_env);
+        const int col = (int)(i - (int64_t)e * p.pix_per_env);
+        int c = 0;
+        while (c + 1 < p.C && col >= p.cams[c + 1].pix_off) ++c;
+        const CamDev &cam = p.cams[c];
+        const int pix = col - cam.pix_off;
+        const int y = pix / cam.out_w, x = pix - y * cam.out_w;
+        uint32_t delta = 0;
+        if (p.span > 1) {
+            const uint4 wl = sensor_words(p.env_offset + (uint32_t)e, (uint32_t)c, 0xFFFFFFFFu, step, p.seed0, p.seed1);
+            int64_t s0 = step - (int64_t)__umulhi(wl.x, p.span);
+            const int64_t first = p.s_first[e];
+            if (s0 < first) s0 = first;
+            if (s0 > step) s0 = step;
+            delta = (uint32_t)(step - s0);
+        }
+        finish_pixel(p, e, c, cam, x, y, src[i], step, delta);
+    }
+}
+
 // Graph replays read the step from device memory; this advances it after each replayed render.
 __global__ void advance_step_kernel(int64_t *step) { *step += 1; }
 
@@ -1068,6 +1095,19 @@ cudaError_t launch_downsample(const RenderParams &p, cudaStream_t s) {
         blocks = std::min<int64_t>(blocks, (int64_t)sms * 8);
     (void)cudaGetLastError();
     downsample_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sensor(const RenderParams &p, const float *src, cudaStream_t s) {
+    const int64_t n = (int64_t)p.E * p.pix_per_env;
+    if (n == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    int64_t blocks = (n + 255) / 256;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
+                                                   cudaSuccess && sms > 0)
+        blocks = std::min<int64_t>(blocks, (int64_t)sms * 8);
+    (void)cudaGetLastError();
+    sensor_kernel<<<(unsigned)blocks, 256, 0, s>>>(p, src);
     return cudaGetLastError();
 }
 

@@ -100,6 +100,8 @@ cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s);
 // Averages the raw images of downsampled cameras and applies the sensor model to them (no-op when
 // p.raw_per_env == 0).  Runs after launch_render of the same parameters.
 cudaError_t launch_downsample(const RenderParams &p, cudaStream_t s);
+// The sensor model alone on pre-sensor depth src [E, pix_per_env] (device, the output layout).
+cudaError_t launch_sensor(const RenderParams &p, const float *src, cudaStream_t s);
 cudaError_t launch_set_first(int64_t *s_first, int32_t E, int64_t step, const uint8_t *mask, cudaStream_t s);
 cudaError_t launch_advance_step(int64_t *step, cudaStream_t s);
 // One launch over several requests: reqs_dev[n_req] parameters in device memory, prefix_dev[n_req + 1]

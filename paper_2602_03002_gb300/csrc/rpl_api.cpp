@@ -938,6 +938,39 @@ RPL_API rpl_status rpl_render(rpl_view_t v, const float *poses, int64_t step, in
     return RPL_OK;
 }
 
+RPL_API rpl_status rpl_sensor_apply(rpl_view_t v, const float *depth_in, int64_t step, int64_t env_offset, void *out,
+                                    void *stream) {
+    NvtxRange range("rpl_sensor_apply");
+    rpl_status st = check_render_args(v, depth_in, env_offset, out);
+    if (st != RPL_OK) return st;
+    if (v->raw_per_env > 0)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_apply: the view has downsampled cameras (give their averaged "
+                                         "depth to a view without downsampling)");
+    if (v->has_last && step != v->last_step && step != v->last_step + 1)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_apply: step %lld after %lld; steps must advance by 0 or 1",
+                    (long long)step, (long long)v->last_step);
+    if (v->E == 0) {
+        v->has_last = true;
+        v->last_step = step;
+        return RPL_OK;
+    }
+    rpl_scene *s = v->scene;
+    DeviceGuard g(s->device);
+    if (pointer_kind(depth_in, s->device) != PTR_DEVICE || pointer_kind(out, s->device) != PTR_DEVICE)
+        return fail(RPL_ERR_INVALID_ARG, "rpl_sensor_apply: input and output must be device memory");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    PrepParams pp;
+    RenderParams rp;
+    st = build_params(v, nullptr, step, env_offset, out, cs, nullptr, nullptr, pp, rp);
+    if (st != RPL_OK) return st;
+    cudaError_t e = launch_sensor(rp, depth_in, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_sensor_apply: launch");
+    v->has_last = true;
+    v->last_step = step;
+    mark_done(v, cs);
+    return RPL_OK;
+}
+
 RPL_API rpl_status rpl_render_counters(rpl_view_t v, const float *poses, int64_t step, int64_t env_offset,
                                        void *out, void *stream, rpl_counters *counters) {
     rpl_status st = check_render_args(v, poses, env_offset, out);

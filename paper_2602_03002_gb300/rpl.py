@@ -87,7 +87,7 @@ class rpl_counters(ctypes.Structure):
 EXPORTS = ["rpl_bvh_build_host", "rpl_bvh8_build_host", "rpl_scene_create", "rpl_link_mesh_add", "rpl_scene_info_get", "rpl_scene_destroy", "rpl_view_create",
            "rpl_cameras_set", "rpl_cameras_randomize", "rpl_side_mask_set", "rpl_sensor_set", "rpl_view_state_size",
            "rpl_view_state_get", "rpl_view_state_set", "rpl_view_layout", "rpl_render", "rpl_view_reset", "rpl_sync",
-           "rpl_render_counters", "rpl_view_timing", "rpl_view_host_async", "rpl_view_kernel_ms", "rpl_view_destroy", "rpl_last_error",
+           "rpl_render_counters", "rpl_view_timing", "rpl_view_host_async", "rpl_sensor_apply", "rpl_view_kernel_ms", "rpl_view_destroy", "rpl_last_error",
            "rpl_version", "rpl_render_static_scratch", "rpl_view_tuning_set", "rpl_view_tuning_get",
            "rpl_view_autotune", "rpl_render_graph", "rpl_server_create", "rpl_server_submit", "rpl_server_wait",
            "rpl_server_cancel", "rpl_server_stats_get", "rpl_server_destroy"]
@@ -126,6 +126,7 @@ def lib() -> ctypes.CDLL:
         "rpl_render_counters": ([P, P, I64, I64, P, P, P], I32),
         "rpl_view_timing": ([P, I32], I32),
         "rpl_view_host_async": ([P, I32], I32),
+        "rpl_sensor_apply": ([P, P, I64, I64, P, P], I32),
         "rpl_view_kernel_ms": ([P, P, I32, P], I32),
         "rpl_view_destroy": ([P], None),
         "rpl_last_error": ([], ctypes.c_char_p),
@@ -313,6 +314,10 @@ def rpl_view_layout(view: int, n_cams: int):
 
 def rpl_render(view: int, poses, step: int, env_offset: int, out, stream=None):
     _check(lib().rpl_render(view, _ptr(poses), int(step), int(env_offset), _ptr(out), _stream_handle(stream)))
+
+
+def rpl_sensor_apply(view: int, depth_in, step: int, env_offset: int, out, stream=None):
+    _check(lib().rpl_sensor_apply(view, _ptr(depth_in), int(step), int(env_offset), _ptr(out), _stream_handle(stream)))
 
 
 def rpl_render_counters(view: int, poses, step: int, env_offset: int, out, stream=None) -> dict:

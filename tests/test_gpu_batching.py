@@ -118,3 +118,43 @@ def test_uneven_four_cameras_vs_oracle(cuda, rpl_lib):
     got = out[rays[:, 0], o[rays[:, 1]] + rays[:, 3] * cam_w[rays[:, 1]] + rays[:, 2]]
     compare_depth(got, ref["depth"], ref["flags"], "uneven cameras")
     assert np.mean(ref["depth"] < 3.0) > 0.3
+
+
+@pytest.mark.slow
+def test_batching_configuration_at_full_size_in_graph_replay(cuda, rpl_lib):
+    """4096 envs x 4 uneven cameras on the 20.48M-triangle terrain, replayed as the CUDA graph the
+    benchmark times with the autotuned launch shape: sampled pixels against the oracle, and the
+    replayed frame equal to a direct render of the same step."""
+    torch = cuda
+    w = W.config_uneven(n_steps=2)
+    scene = rpl_lib.Scene.from_workload(w)
+    view = rpl_lib.View.from_workload(scene, w)
+    direct = rpl_lib.View.from_workload(scene, w)
+    poses = torch.from_numpy(w.poses).cuda()
+    out = view.out_tensor()
+    best, _ = rpl_lib.rpl_view_autotune(view.h, poses[0], 0, 0, out, None, 1)
+    rpl_lib.rpl_view_tuning_set(direct.h, **best)
+    view.reset(None, 0)
+    buf = poses[0].clone()
+    frames = []
+    for s in range(2):
+        buf.copy_(poses[s])
+        assert rpl_lib.rpl_render_graph(view.h, buf, 0, out) == s
+        torch.cuda.synchronize()
+        frames.append(out.cpu().numpy().copy())
+        assert torch.equal(out, direct.render(poses[s], s)), s
+    view.sync()
+    offs, total = view.layout()
+    rng = np.random.default_rng(31)
+    n = 240
+    c = rng.integers(0, 4, n)
+    cw = np.array([cam.width for cam in w.cameras])
+    ch = np.array([cam.height for cam in w.cameras])
+    rays = np.stack([rng.integers(0, w.n_envs, n), c, (rng.random(n) * cw[c]).astype(np.int64),
+                     (rng.random(n) * ch[c]).astype(np.int64)], 1).astype(np.int64)
+    osc = oracle.OracleScene.from_workload(w)
+    ref = osc.render(w.cameras, w.poses, 1, rays, w.sensor)
+    o = np.asarray(offs)
+    got = frames[1][rays[:, 0], o[rays[:, 1]] + rays[:, 3] * cw[rays[:, 1]] + rays[:, 2]]
+    compare_depth(got, ref["depth"], ref["flags"], "batching full size")
+    assert np.mean(ref["depth"] < 3.0) > 0.3
