@@ -10,7 +10,9 @@ Variants (``--variant``):
   perception the paper's perception settings: 4096 envs x 2 cameras ray cast at 240x135 and averaged
              to 48x27 (101 x 69 deg FOV), per-env camera pose and FOV randomisation, side masking by
              terrain kind, sensor preset sigma = 0.1 depth, 5 % dropout, latency 0-3;
-  serving    Poisson request streams from 4 trainers through the continuous-batching server.
+  serving    Poisson request streams from 4 trainers through the continuous-batching server;
+  table1     the paper's Table 1 setting (1024 envs, 240x135, 1 / 2 / 4 cameras): time per render
+             and device memory per camera count.
 One step = the whole path over all envs with the next resident pose set: rpl_render (prep + render
 kernels), or one graph replay for ``batching``.  The launch shape is chosen by the library's
 autotuner before timing.  Rank 0 prints one JSON line.  ``--impl reference`` times the FP64 CPU
@@ -48,7 +50,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variant", default="plain", choices=["plain", "precision", "batching", "perception", "serving"])
+    ap.add_argument("--variant", default="plain",
+                    choices=["plain", "precision", "batching", "perception", "serving", "table1"])
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--tiles", type=int, default=20)
     ap.add_argument("--pose-sets", type=int, default=8)
@@ -74,6 +77,8 @@ def workload(args, rank):
         return W.config_uneven(n_steps=args.pose_sets, n_envs=args.envs, tiles=args.tiles, seed=rank)
     if args.variant == "perception":
         return W.config_perception(n_steps=args.pose_sets, n_envs=args.envs, tiles=args.tiles, seed=rank)
+    if args.variant == "table1":
+        return W.config_perception(n_steps=args.pose_sets, n_envs=1024, tiles=args.tiles, seed=rank)
     w = W.config_scale(n_steps=args.pose_sets, n_envs=args.envs, tiles=args.tiles, seed=rank)
     if args.variant == "precision":
         w.sensor.out_dtype = 1
@@ -103,7 +108,9 @@ def workload_name(w, variant, bvh):
         "plain": "FP32 depth", "precision": "FP16 depth",
         "batching": "FP32 depth, one CUDA-graph replay per step",
         "perception": "FP32 depth, raw images block-averaged before the sensor, per-env camera pose/FOV "
-                      "randomisation, side masking (cols %s by mode)" % (tuple(w.rsm_cols),)}[variant]
+                      "randomisation, side masking (cols %s by mode)" % (tuple(w.rsm_cols),),
+        "table1": "FP32 depth, the paper's Table 1 setting (1024 envs, 240x135 averaged to 48x27)",
+        "serving": "FP32 depth, requests served by the continuous-batching server"}[variant]
     return ("%s: %d envs x cams (%s px); terrain %d tris (tiles of 8x8 m at 0.05 m: stairs 0.22/0.25/0.30 m run, "
             "20 deg slopes, stepping stones); %d links x %d-tri meshes; %s; %s"
             % (variant, w.n_envs, cams, len(w.terrain_tris), w.n_links, len(w.link_tris[0]), sensor, form))
@@ -274,12 +281,18 @@ def run_ours(args):
     w = workload(args, rank)
     env_offset = rank * args.envs
     kind = bvh_kind(args, rpl)
+    free0 = torch.cuda.mem_get_info(dev)[0]
     t0 = time.perf_counter()
     scene = rpl.Scene(w.terrain_verts, w.terrain_tris, device=dev, bvh_kind=kind)
     for l, (v_, t_) in enumerate(zip(w.link_verts, w.link_tris)):
         scene.add_link(l, v_, t_)
     build_s = time.perf_counter() - t0
+    free1 = torch.cuda.mem_get_info(dev)[0]
     view = rpl.View.from_workload(scene, w)
+    free2 = torch.cuda.mem_get_info(dev)[0]
+    vram = {"scene_gb": (free0 - free1) / 1e9, "view_gb": (free1 - free2) / 1e9,
+            "note": "device memory taken by the library's scene (BVHs) and view (transforms, ring, raw and "
+                    "staging buffers), from cudaMemGetInfo around their creation"}
     info = scene.info()
     stream = torch.cuda.Stream(dev)
     poses = torch.from_numpy(w.poses).to(f"cuda:{dev}")
@@ -419,6 +432,7 @@ def run_ours(args):
                      "per_ray": {k: cnt[k] / rays for k in ("terrain_nodes", "terrain_tris", "link_boxes",
                                                             "link_nodes", "link_tris")}},
         "clocks": ck,
+        "vram": vram,
         "e2e": e2e,
         "scene": {"terrain_tris": info["terrain_tris"], "terrain_nodes": info["terrain_nodes"],
                   "terrain_depth": info["terrain_depth"], "terrain_bytes": info["terrain_bytes"],
@@ -558,12 +572,76 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_table1(args):
+    """The setting of the paper's Table 1 (1024 envs, 240x135 depth, 1 / 2 / 4 cameras) with the
+    perception workload's cameras, randomisation and sensor: time per render and device memory for
+    each camera count.  The paper's own figures are training-iteration times on an L40S, not render
+    times, so they are context only."""
+    import torch
+    from paper_2602_03002_gb300 import build as B, rpl, workloads as W
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    B.build()
+    envs = 1024
+    w = W.config_perception(n_steps=args.pose_sets, n_envs=envs, tiles=args.tiles, n_cams=4)
+    free0 = torch.cuda.mem_get_info(local)[0]
+    scene = rpl.Scene(w.terrain_verts, w.terrain_tris, device=local, bvh_kind=bvh_kind(args, rpl))
+    for l, (v_, t_) in enumerate(zip(w.link_verts, w.link_tris)):
+        scene.add_link(l, v_, t_)
+    scene_gb = (free0 - torch.cuda.mem_get_info(local)[0]) / 1e9
+    poses = torch.from_numpy(w.poses).cuda()
+    S = poses.shape[0]
+    rows = []
+    for n_cams in (1, 2, 4):
+        free1 = torch.cuda.mem_get_info(local)[0]
+        view = rpl.View(scene, envs, w.n_links)
+        view.set_cameras(w.cameras[:n_cams], w.per_env_intrinsics[:, :n_cams])
+        view.randomize_cameras(w.mount_delta[:, :n_cams])
+        view.set_side_mask(w.rsm_cols, w.rsm_modes)
+        view.set_sensor(w.sensor)
+        out = view.out_tensor()
+        view_gb = (free1 - torch.cuda.mem_get_info(local)[0]) / 1e9
+        tuning, _ = rpl.rpl_view_autotune(view.h, poses[0], 0, 0, out, None, 2)
+        view.reset(None, 0)
+        for s in range(args.warmup):
+            rpl.rpl_render(view.h, poses[s % S], s, 0, out, None)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for s in range(args.warmup, args.warmup + args.steps):
+            rpl.rpl_render(view.h, poses[s % S], s, 0, out, None)
+        b.record()
+        torch.cuda.synchronize()
+        view.sync()
+        ms = a.elapsed_time(b) / args.steps
+        rays = envs * n_cams * 240 * 135
+        rows.append({"n_cam": n_cams, "ms_per_render": ms, "grays_per_s": rays / ms / 1e6,
+                     "depth_frames_per_s": envs * n_cams / (ms / 1e3), "view_vram_gb": view_gb, "tuning": tuning})
+        view.close()
+    two = rows[1]
+    line = {"metric": METRIC, "value": two["grays_per_s"], "unit": "Grays/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": two["ms_per_render"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "variant": "table1",
+            "config": {"workload": "the paper's Table 1 setting: 1024 envs, 240x135 ray cast (averaged to 48x27), "
+                                   "1 / 2 / 4 cameras, scale terrain (%d tris), perception randomisation and sensor; "
+                                   "value = the 2-camera row" % len(w.terrain_tris)},
+            "table1": rows, "scene_vram_gb": scene_gb,
+            "paper_context": "Table 1 (one L40S, 1024 envs, 240x135): 1.3 / 1.5 / 1.9 s per training iteration "
+                             "and 13.3 / 14.6 / 17.3 GB for 1 / 2 / 4 cameras; iteration times include physics "
+                             "and learning, so they are not render times"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.variant == "serving":
         run_serving(args)
+    elif args.variant == "table1":
+        run_table1(args)
     else:
         run_ours(args)
 
