@@ -674,7 +674,9 @@ __device__ __forceinline__ int descend_wide(const float4 *__restrict__ nodes, in
 
 // Closest hit in the wide terrain BVH.  The stack holds groups of inner children still to visit,
 // (first child index, imask | remaining traversal-order mask << 8); children are taken in the order
-// slot ^ octant(d), roughly front to back.  Leaf children of a node are tested when it is visited.
+// slot ^ octant(d), roughly front to back.  Leaf children of a node are tested when it is visited:
+// postponing them as the binary traversal does was 40 % slower here, since the bound then shrinks
+// late and the coarse octant order visits many more nodes before the first hit.
 template <bool kCount>
 __device__ __forceinline__ bool traverse8(const float4 *__restrict__ nodes, const float4 *__restrict__ tris, int root,
                                           const Ray &r, int oct, float &tmax, bool &hit, Counts &cnt) {
