@@ -126,10 +126,15 @@ def peaks():
 
 
 def kernel_hash():
+    """Hash of the kernel sources with line comments and blank lines removed, so that a change of
+    comments alone keeps a traffic capture valid."""
     h = hashlib.sha256()
     for f in ("render.cu", "render.h", "bvh.h", "bvh4.h", "bvh8.h"):
-        with open(os.path.join(ROOT, "paper_2602_03002_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2602_03002_gb300", "csrc", f), encoding="utf-8") as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].strip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
