@@ -100,8 +100,7 @@ def lib() -> ctypes.CDLL:
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise RuntimeError("librpl.so is not built (%s); run paper_2602_03002_gb300.build.build() "
-                           "or __graft_entry__.build()" % LIB_PATH)
+        raise RuntimeError("librpl.so is not built (%s); run paper_2602_03002_gb300.build.build()" % LIB_PATH)
     L = ctypes.CDLL(LIB_PATH)
     P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     sig = {
