@@ -30,6 +30,45 @@ def test_library_exports_every_declared_symbol(rpl_lib):
     assert rpl_lib.lib().rpl_version() == 1
 
 
+def test_header_is_plain_c_and_links(rpl_lib, tmp_path):
+    """include/rpl.h compiles as C11 (no C++ or torch types at the boundary) and a C program links
+    against librpl.so and calls it: version, argument errors and the error message, no GPU needed."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "rpl.h"
+int main(void) {
+    if (rpl_version() != 1) return 1;
+    rpl_scene_t s = 0;
+    if (rpl_scene_create(0, 0, 0, 0, 0, 0) != RPL_ERR_INVALID_ARG) return 2;
+    if (strstr(rpl_last_error(), "out is NULL") == 0) return 3;
+    rpl_view_t v = 0;
+    if (rpl_view_create(s, 4, 2, &v) != RPL_ERR_INVALID_ARG || v != 0) return 4;
+    rpl_camera cam;
+    memset(&cam, 0, sizeof cam);
+    if (rpl_cameras_set(0, &cam, 1, 0) != RPL_ERR_INVALID_ARG) return 5;
+    if (rpl_render(0, 0, 0, 0, 0, 0) != RPL_ERR_INVALID_ARG) return 6;
+    int64_t n = 0;
+    if (rpl_view_state_size(0, &n) != RPL_ERR_INVALID_ARG) return 7;
+    printf("ok\n");
+    return 0;
+}
+""")
+    exe = tmp_path / "abi"
+    lib_dir = os.path.dirname(rpl_lib.LIB_PATH)
+    r = subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-o", str(exe), "-L", lib_dir, "-lrpl", "-Wl,-rpath," + lib_dir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
+
+
 def test_scene_create_fails_cleanly_without_gpu(rpl_lib):
     import torch
     if torch.cuda.is_available():
