@@ -15,6 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librpl.so")
+# bounds-checked build (every node and triangle index tested before it is read; see render.cu)
+LIB_CHECKED = os.path.join(HERE, "librpl_checked.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -29,26 +31,29 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build librpl.so")
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "rpl.h"),
                                                                   os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    """Compile and link librpl.so unless it is up to date. Returns its path."""
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, checked: bool = False) -> str:
+    """Compile and link librpl.so (or, with checked, librpl_checked.so, whose kernels test every node
+    and triangle index against its array) unless it is up to date. Returns its path."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and not _stale(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    out_dir = os.path.join(BUILD, "checked") if checked else BUILD
+    os.makedirs(out_dir, exist_ok=True)
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden,-ffp-contract=off",
-              "-I", os.path.join(ROOT, "include")]
+              "-I", os.path.join(ROOT, "include")] + (["-DRPL_CHECKED"] if checked else [])
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(out_dir, src + ".o")
         cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + common
         if src.endswith(".cu"):
             cmd += ARCH + ["-lineinfo"]
@@ -63,13 +68,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("linking librpl.so failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -144,6 +144,9 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
         pp.link_root = si.link_root;
         pp.tnodes = si.tnodes;
         pp.bvh_kind = si.bvh_kind;
+#ifdef RPL_CHECKED
+        pp.n_tnodes = si.n_tnodes;
+#endif
         pp.intr = nullptr;
         pp.link_xf = reinterpret_cast<float4 *>(sb);
         pp.link_box = reinterpret_cast<float4 *>(sb + off_box);
@@ -159,6 +162,12 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
             rp.tnodes = si.tnodes;
             rp.ttris = si.ttris;
             rp.bvh_kind = si.bvh_kind;
+#ifdef RPL_CHECKED
+            rp.n_tnodes = si.n_tnodes;
+            rp.n_ttris = si.n_ttris;
+            rp.n_lnodes = si.n_lnodes;
+            rp.n_ltris = si.n_ltris;
+#endif
             rp.out_dtype = RPL_OUT_F32;
             rp.lnodes = si.lnodes;
             rp.ltris = si.ltris;

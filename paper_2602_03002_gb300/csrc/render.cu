@@ -28,6 +28,30 @@
 namespace rpl {
 namespace {
 
+// Bounds-checked build (RPL_CHECKED, librpl_checked.so): every node and triangle index is tested
+// against the length of its array before it is read; a violation sets bit 4 of the view's error
+// word and ends that ray's walk instead of reading.  In the normal build the macros below expand to
+// nothing, so its kernels are exactly the unchecked code.
+#ifdef RPL_CHECKED
+__device__ __forceinline__ bool in_range(int64_t i, int64_t n) { return (uint64_t)i < (uint64_t)n; }
+constexpr uint32_t kErrBounds = 4;
+#define RPL_CK_PARAMS , int64_t ck_nodes, int64_t ck_tris, uint32_t &ck_err
+#define RPL_CK_ARGS(n, t, e) , (n), (t), (e)
+#define RPL_CK_NODE(i, on_fail)                                                                        \
+    if (!in_range((i), ck_nodes)) {                                                                  \
+        ck_err |= kErrBounds;                                                                        \
+        on_fail;                                                                                     \
+    }
+#define RPL_CK_DESCEND_PARAMS , int64_t ck_nodes
+#define RPL_CK_DESCEND_ARGS(n) , (n)
+#else
+#define RPL_CK_PARAMS
+#define RPL_CK_ARGS(n, t, e)
+#define RPL_CK_NODE(i, on_fail)
+#define RPL_CK_DESCEND_PARAMS
+#define RPL_CK_DESCEND_ARGS(n)
+#endif
+
 // ---------------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
 //   (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
@@ -96,7 +120,7 @@ __device__ __forceinline__ bool boxes_overlap(float alx, float ahx, float aly, f
 // Deepest binary node below `node` that holds everything inside the AABB [lo, hi]: descend while
 // exactly one child's box meets the AABB and that child is an inner node.
 __device__ __forceinline__ int descend_binary(const float4 *__restrict__ nodes, int node, const float lo[3],
-                                              const float hi[3]) {
+                                              const float hi[3] RPL_CK_DESCEND_PARAMS) {
 #pragma unroll 1
     for (int depth = 0; depth < kStackDepth; ++depth) {
         const float4 *n = nodes + 4 * node;
@@ -108,6 +132,9 @@ __device__ __forceinline__ int descend_binary(const float4 *__restrict__ nodes, 
         if (h0 && !h1 && n3.x >= 0) next = n3.x;
         if (h1 && !h0 && n3.y >= 0) next = n3.y;
         if (next < 0) break;
+#ifdef RPL_CHECKED
+        if (!in_range(next, ck_nodes)) break;
+#endif
         node = next;
     }
     return node;
@@ -115,15 +142,19 @@ __device__ __forceinline__ int descend_binary(const float4 *__restrict__ nodes, 
 
 // The same for the eight-wide layout (defined with the wide traversal below).
 __device__ __forceinline__ int descend_wide(const float4 *__restrict__ nodes, int node, const float lo[3],
-                                            const float hi[3]);
-__device__ __forceinline__ int descend4(const float4 *__restrict__ nodes, int node, const float lo[3], const float hi[3]);
+                                            const float hi[3] RPL_CK_DESCEND_PARAMS);
+__device__ __forceinline__ int descend4(const float4 *__restrict__ nodes, int node, const float lo[3],
+                                        const float hi[3] RPL_CK_DESCEND_PARAMS);
 
 // Entry node of the terrain walk for the layout `kind` (rpl_bvh_kind).
 __device__ __forceinline__ int descend_any(int kind, const float4 *__restrict__ nodes, int node, const float lo[3],
-                                           const float hi[3]) {
-    if (kind == RPL_BVH8Q8) return descend_wide(nodes, node, lo, hi);
-    if (kind == RPL_BVH4) return descend4(nodes, node, lo, hi);
-    return descend_binary(nodes, node, lo, hi);
+                                           const float hi[3] RPL_CK_DESCEND_PARAMS) {
+#ifdef RPL_CHECKED
+    if (!in_range(node, ck_nodes)) node = 0;
+#endif
+    if (kind == RPL_BVH8Q8) return descend_wide(nodes, node, lo, hi RPL_CK_DESCEND_ARGS(ck_nodes));
+    if (kind == RPL_BVH4) return descend4(nodes, node, lo, hi RPL_CK_DESCEND_ARGS(ck_nodes));
+    return descend_binary(nodes, node, lo, hi RPL_CK_DESCEND_ARGS(ck_nodes));
 }
 
 __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepParams p) {
@@ -252,7 +283,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
 
     // 2) terrain entry node: descend while exactly one child's box meets the view volume's AABB and
     //    that child is an inner node; nothing in the other subtrees can be hit by this camera's rays
-    const int node = descend_any(p.bvh_kind, p.tnodes, 0, flo, fhi);
+    const int node = descend_any(p.bvh_kind, p.tnodes, 0, flo, fhi RPL_CK_DESCEND_ARGS(p.n_tnodes));
     // 3) latency of this (env, camera, step): k = (w0 (Lmax + 1)) >> 32 from the word with pixel field
     //    0xFFFFFFFF; source step s' = max(s - k, first step since reset); stored as s - s'
     uint32_t delta = 0;
@@ -362,7 +393,13 @@ struct Counts {
 
 template <bool kSplit, bool kCount>
 __device__ __forceinline__ void leaf(const float4 *__restrict__ tris, int first, int count, const Ray &r,
-                                     float &tmax, bool &hit, Counts &cnt) {
+                                     float &tmax, bool &hit, Counts &cnt RPL_CK_PARAMS) {
+#ifdef RPL_CHECKED
+    if (first < 0 || !in_range((int64_t)first + count - 1, ck_tris)) {
+        ck_err |= kErrBounds;
+        return;
+    }
+#endif
 #pragma unroll 1
     for (int i = first; i < first + count; ++i) {
         const float4 a = __ldg(tris + 3 * i), b = __ldg(tris + 3 * i + 1), c = __ldg(tris + 3 * i + 2);
@@ -393,7 +430,7 @@ __device__ __forceinline__ int stack_pop(const int *stack, int &sp) { return sp 
 // warp's (ray, link) pairs so that link BVHs are traversed with full warps.)
 template <bool kSplit, bool kCount>
 __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const float4 *__restrict__ tris, int root,
-                                         const Ray &r, float &tmax, bool &hit, Counts &cnt) {
+                                         const Ray &r, float &tmax, bool &hit, Counts &cnt RPL_CK_PARAMS) {
     int stack_node[kStackDepth];
     int sp = 0;
     bool ok = true;
@@ -404,6 +441,7 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
     for (;;) {
 #pragma unroll 1
         while (cur >= 0) {
+            RPL_CK_NODE(cur, cur = kDone; break)
             const float4 *n = nodes + 4 * cur;
             const float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2);
             const int4 n3 = __ldg(reinterpret_cast<const int4 *>(n + 3));
@@ -445,7 +483,7 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
 #pragma unroll 1
         while (pending < 0) {
             const int ref = ~pending;
-            leaf<kSplit, kCount>(tris, ref >> 3, (ref & 7) + 1, r, tmax, hit, cnt);
+            leaf<kSplit, kCount>(tris, ref >> 3, (ref & 7) + 1, r, tmax, hit, cnt RPL_CK_ARGS(ck_nodes, ck_tris, ck_err));
             pending = 0;
             if (cur < 0 && cur != kDone) {
                 pending = cur;
@@ -472,7 +510,8 @@ __device__ __forceinline__ Node4 load4(const float4 *__restrict__ nodes, int i) 
 
 // Deepest four-wide node below `node` that holds everything inside the AABB [lo, hi]: descend while
 // exactly one child box meets the AABB and that child is an inner node (unused slots sit at 1e30).
-__device__ __forceinline__ int descend4(const float4 *__restrict__ nodes, int node, const float lo[3], const float hi[3]) {
+__device__ __forceinline__ int descend4(const float4 *__restrict__ nodes, int node, const float lo[3],
+                                        const float hi[3] RPL_CK_DESCEND_PARAMS) {
 #pragma unroll 1
     for (int depth = 0; depth < kStackDepth; ++depth) {
         const Node4 n = load4(nodes, node);
@@ -483,6 +522,9 @@ __device__ __forceinline__ int descend4(const float4 *__restrict__ nodes, int no
         if ((int)o0 + (int)o1 + (int)o2 + (int)o3 != 1) break;
         const int c = o0 ? n.ch.x : (o1 ? n.ch.y : (o2 ? n.ch.z : n.ch.w));
         if (c < 0) break;
+#ifdef RPL_CHECKED
+        if (!in_range(c, ck_nodes)) break;
+#endif
         node = c;
     }
     return node;
@@ -504,7 +546,7 @@ __device__ __forceinline__ void cmp_swap(float &ta, int &ea, float &tb, int &eb)
 // are sorted by entry distance, the nearest is visited next and the others pushed far to near.
 template <bool kCount>
 __device__ __forceinline__ bool traverse4(const float4 *__restrict__ nodes, const float4 *__restrict__ tris, int root,
-                                          const Ray &r, float &tmax, bool &hit, Counts &cnt) {
+                                          const Ray &r, float &tmax, bool &hit, Counts &cnt RPL_CK_PARAMS) {
     int stack_node[kStackDepth];
     int sp = 0;
     bool ok = true;
@@ -515,6 +557,7 @@ __device__ __forceinline__ bool traverse4(const float4 *__restrict__ nodes, cons
     for (;;) {
 #pragma unroll 1
         while (cur >= 0) {
+            RPL_CK_NODE(cur, cur = kDone; break)
             const Node4 n = load4(nodes, cur);
             if (kCount) ++cnt.nodes;
             float t0 = slab(r, n.lx.x, n.hx.x, n.ly.x, n.hy.x, n.lz.x, n.hz.x, tmax);
@@ -554,7 +597,7 @@ __device__ __forceinline__ bool traverse4(const float4 *__restrict__ nodes, cons
 #pragma unroll 1
         while (pending < 0) {
             const int ref = ~pending;
-            leaf<true, kCount>(tris, ref >> 3, (ref & 7) + 1, r, tmax, hit, cnt);
+            leaf<true, kCount>(tris, ref >> 3, (ref & 7) + 1, r, tmax, hit, cnt RPL_CK_ARGS(ck_nodes, ck_tris, ck_err));
             pending = 0;
             if (cur < 0 && cur != kDone) {
                 pending = cur;
@@ -650,7 +693,7 @@ __device__ __forceinline__ void wide_child_box(const WideNode &n, int s, float l
 // Deepest wide node below `node` that holds everything inside the AABB [lo, hi]: descend while
 // exactly one slot's box meets the AABB and that slot is an inner node.
 __device__ __forceinline__ int descend_wide(const float4 *__restrict__ nodes, int node, const float lo[3],
-                                            const float hi[3]) {
+                                            const float hi[3] RPL_CK_DESCEND_PARAMS) {
 #pragma unroll 1
     for (int depth = 0; depth < kStackDepth; ++depth) {
         const WideNode n = load_wide(nodes, node);
@@ -667,6 +710,9 @@ __device__ __forceinline__ int descend_wide(const float4 *__restrict__ nodes, in
         }
         const uint32_t imask = n.a.w >> 24;
         if (n_hit != 1 || !((imask >> slot) & 1u)) break;
+#ifdef RPL_CHECKED
+        if (!in_range((int64_t)n.b.x + (meta_byte(n, slot) & 0x7Fu), ck_nodes)) break;
+#endif
         node = (int)n.b.x + (int)(meta_byte(n, slot) & 0x7Fu);
     }
     return node;
@@ -679,12 +725,13 @@ __device__ __forceinline__ int descend_wide(const float4 *__restrict__ nodes, in
 // late and the coarse octant order visits many more nodes before the first hit.
 template <bool kCount>
 __device__ __forceinline__ bool traverse8(const float4 *__restrict__ nodes, const float4 *__restrict__ tris, int root,
-                                          const Ray &r, int oct, float &tmax, bool &hit, Counts &cnt) {
+                                          const Ray &r, int oct, float &tmax, bool &hit, Counts &cnt RPL_CK_PARAMS) {
     uint2 stack[kStackDepth];
     int sp = 0;
     int node = root;
 #pragma unroll 1
     for (;;) {
+        RPL_CK_NODE(node, return true)
         const WideNode n = load_wide(nodes, node);
         if (kCount) ++cnt.nodes;
         const uint32_t hits = wide_hits(n, r, tmax);
@@ -696,7 +743,8 @@ __device__ __forceinline__ bool traverse8(const float4 *__restrict__ nodes, cons
             const int s = (__ffs(leaves) - 1) ^ oct;
             leaves &= leaves - 1;
             const uint32_t m = meta_byte(n, s);
-            leaf<true, kCount>(tris, (int)n.b.y + (int)((m >> 2) & 31u), (int)(m & 3u) + 1, r, tmax, hit, cnt);
+            leaf<true, kCount>(tris, (int)n.b.y + (int)((m >> 2) & 31u), (int)(m & 3u) + 1, r, tmax, hit,
+                               cnt RPL_CK_ARGS(ck_nodes, ck_tris, ck_err));
         }
         uint32_t inner = oct_permute(hits & imask, oct);
         uint32_t base = n.b.x, im = imask;
@@ -843,7 +891,10 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
             thi[a] = hi + slack;
         }
     }
-    const int entry = descend_any(kKind, p.tnodes, __float_as_int(CV.z), tlo, thi);
+    const int entry = descend_any(kKind, p.tnodes, __float_as_int(CV.z), tlo, thi RPL_CK_DESCEND_ARGS(p.n_tnodes));
+#ifdef RPL_CHECKED
+    uint32_t ck_err = 0;
+#endif
     uint64_t link_mask = 0;
 #pragma unroll 1
     for (uint64_t mk = cam_mask; mk; mk &= mk - 1) {
@@ -878,18 +929,18 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
                                       X2.x * d.x + X2.y * d.y + X2.z * d.z);
         Ray lr;
         make_ray(lr, ob, make_float3(0.f, 0.f, 0.f), db);
-        ok &= traverse<false, kCount>(p.lnodes, p.ltris, root, lr, tmax, hit, cnt_l);
+        ok &= traverse<false, kCount>(p.lnodes, p.ltris, root, lr, tmax, hit, cnt_l RPL_CK_ARGS(p.n_lnodes, p.n_ltris, ck_err));
     }
     };
     // 2) static terrain, bounded by the closest hit so far
     auto query_terrain = [&]() {
         if (kKind == RPL_BVH8Q8) {
             const int oct = (d.x < 0.f ? 1 : 0) | (d.y < 0.f ? 2 : 0) | (d.z < 0.f ? 4 : 0);
-            ok &= traverse8<kCount>(p.tnodes, p.ttris, entry, ray, oct, tmax, hit, cnt_t);
+            ok &= traverse8<kCount>(p.tnodes, p.ttris, entry, ray, oct, tmax, hit, cnt_t RPL_CK_ARGS(p.n_tnodes, p.n_ttris, ck_err));
         } else if (kKind == RPL_BVH4) {
-            ok &= traverse4<kCount>(p.tnodes, p.ttris, entry, ray, tmax, hit, cnt_t);
+            ok &= traverse4<kCount>(p.tnodes, p.ttris, entry, ray, tmax, hit, cnt_t RPL_CK_ARGS(p.n_tnodes, p.n_ttris, ck_err));
         } else {
-            ok &= traverse<true, kCount>(p.tnodes, p.ttris, entry, ray, tmax, hit, cnt_t);
+            ok &= traverse<true, kCount>(p.tnodes, p.ttris, entry, ray, tmax, hit, cnt_t RPL_CK_ARGS(p.n_tnodes, p.n_ttris, ck_err));
         }
     };
     if (p.terrain_first) {
@@ -900,6 +951,9 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
         query_terrain();
     }
     if (!ok) atomicOr(p.err, 1);
+#ifdef RPL_CHECKED
+    if (ck_err) atomicOr(p.err, (int)ck_err);
+#endif
 
     const float z = hit ? fminf(m * tmax, cam.d_max) : cam.d_max;
     if (cam.ds > 1) {

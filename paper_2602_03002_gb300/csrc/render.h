@@ -31,6 +31,9 @@ struct PrepParams {
     const float *poses;        // [E, L, 7]
     const float4 *link_root;   // [RPL_MAX_LINKS * 2] link-frame root boxes (lo, hi)
     const float4 *tnodes;      // terrain BVH nodes in the layout of bvh_kind
+#ifdef RPL_CHECKED
+    int64_t n_tnodes;          // number of terrain nodes (bounds-checked build)
+#endif
     int32_t bvh_kind;          // rpl_bvh_kind: binary (bvh.h), eight-wide quantised (bvh8.h), four-wide (bvh4.h)
     const float *intr;         // [E, C, 4] per-env intrinsics or null
     const float *mount_dr;     // [E, C, 7] per-env mount perturbation (dp, dq xyzw) or null
@@ -62,6 +65,9 @@ struct RenderParams {
     int32_t out_dtype;      // rpl_out_dtype of `out`
     const float4 *lnodes;   // all link BVH nodes
     const float4 *ltris;    // all link triangles
+#ifdef RPL_CHECKED
+    int64_t n_tnodes, n_ttris, n_lnodes, n_ltris;   // element counts of the four arrays (checked build)
+#endif
     const float4 *link_xf;
     const float4 *link_box;
     const float4 *cam_xf;
@@ -87,7 +93,7 @@ struct RenderParams {
     int32_t rsm_cols[3];            // columns masked on each side per mode
     const int64_t *s_first;         // [E]
     void *out;                      // [E, pix_per_env] of out_dtype
-    int32_t *err;                   // error word (bit 0: traversal stack overflow)
+    int32_t *err;                   // error word (1: traversal stack overflow, 4: index out of range)
     unsigned long long *counters;   // rpl_counters fields, or null
     // fused launches only (render_multi_kernel): tiles of this request still running, and a word in
     // host-mapped memory set to 1 when the last of them has stored its pixels; null when unused

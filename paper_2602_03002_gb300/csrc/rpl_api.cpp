@@ -733,6 +733,13 @@ static int32_t fill_cams(const rpl_view *v, CamDev *out) {
 
 static size_t out_elem_bytes(const rpl_view *v) { return v->sensor.out_dtype == RPL_OUT_F32 ? 4 : 2; }
 
+// Terrain nodes held by the device array, in units of the scene's node layout.
+static int64_t terrain_node_count(const rpl_scene *s) {
+    const size_t node = s->opts.bvh_kind == RPL_BVH8Q8 ? sizeof(Bvh8Node)
+                        : s->opts.bvh_kind == RPL_BVH4 ? sizeof(Bvh4Node) : sizeof(BvhNode);
+    return (int64_t)(s->t_nodes.bytes / node);
+}
+
 // Marks the end of the work just enqueued for `v` on `st`.
 static void mark_done(rpl_view *v, cudaStream_t st) {
     if (cudaEventRecord(v->done, st) == cudaSuccess) v->has_done = true;
@@ -756,6 +763,9 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
     pp.link_root = s->l_roots.as<const float4>();
     pp.tnodes = s->t_nodes.as<const float4>();
     pp.bvh_kind = s->opts.bvh_kind;
+#ifdef RPL_CHECKED
+    pp.n_tnodes = terrain_node_count(s);
+#endif
     pp.intr = v->intr.p ? v->intr.as<const float>() : nullptr;
     pp.mount_dr = v->mount_dr.p ? v->mount_dr.as<const float>() : nullptr;
     for (int l = 0; l < RPL_MAX_LINKS; ++l) pp.lroot[l] = l < v->L ? s->l_root[l] : -1;
@@ -781,6 +791,12 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
     rp.out_dtype = v->sensor.out_dtype;
     rp.lnodes = s->l_nodes.as<const float4>();
     rp.ltris = s->l_tris.as<const float4>();
+#ifdef RPL_CHECKED
+    rp.n_tnodes = terrain_node_count(s);
+    rp.n_ttris = (int64_t)(s->t_tris.bytes / sizeof(BvhTri));
+    rp.n_lnodes = (int64_t)(s->l_nodes.bytes / sizeof(BvhNode));
+    rp.n_ltris = (int64_t)(s->l_tris.bytes / sizeof(BvhTri));
+#endif
     rp.link_xf = v->link_xf.as<const float4>();
     rp.link_box = v->link_box.as<const float4>();
     rp.cam_xf = v->cam_xf.as<const float4>();
@@ -857,7 +873,7 @@ static rpl_status check_render_args(rpl_view *v, const float *poses, int64_t env
         return fail(RPL_ERR_INVALID_ARG, "rpl_render: poses and output must be 4-byte aligned");
     if (*v->err_host != 0)
         return fail(RPL_ERR_DEVICE_FAULT, "rpl_render: an earlier kernel on this view recorded error 0x%x "
-                    "(traversal stack overflow); call rpl_sync", *v->err_host);
+                    "(1: stack overflow, 4: index out of range); call rpl_sync", *v->err_host);
     return RPL_OK;
 }
 
@@ -1119,7 +1135,8 @@ RPL_API rpl_status rpl_sync(rpl_view_t v) {
     int32_t w = *(volatile int32_t *)v->err_host;
     if (w != 0) {
         *v->err_host = 0;
-        return fail(RPL_ERR_DEVICE_FAULT, "rpl_sync: a render kernel recorded error 0x%x (traversal stack overflow)", w);
+        return fail(RPL_ERR_DEVICE_FAULT, "rpl_sync: a render kernel recorded error 0x%x (1: traversal stack overflow, "
+                    "4: node or triangle index out of range)", w);
     }
     return RPL_OK;
 }
@@ -1374,6 +1391,10 @@ bool scene_inputs(const rpl_scene *s, SceneInputs *out) {
     out->device = s->device;
     out->bvh_kind = s->opts.bvh_kind;
     out->tnodes = s->t_nodes.as<const float4>();
+    out->n_tnodes = terrain_node_count(s);
+    out->n_ttris = (int64_t)(s->t_tris.bytes / sizeof(BvhTri));
+    out->n_lnodes = (int64_t)(s->l_nodes.bytes / sizeof(BvhNode));
+    out->n_ltris = (int64_t)(s->l_tris.bytes / sizeof(BvhTri));
     out->ttris = s->t_tris.as<const float4>();
     out->lnodes = s->l_nodes.as<const float4>();
     out->ltris = s->l_tris.as<const float4>();

@@ -12,6 +12,7 @@ struct SceneInputs {
     int device;
     int bvh_kind;   // rpl_bvh_kind of the terrain BVH
     const float4 *tnodes, *ttris, *lnodes, *ltris, *link_root;
+    int64_t n_tnodes, n_ttris, n_lnodes, n_ltris;   // element counts of the four arrays
     int32_t lroot[RPL_MAX_LINKS];
 };
 

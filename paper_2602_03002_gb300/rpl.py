@@ -14,7 +14,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librpl.so")
+# RPL_CHECKED=1 selects the bounds-checked build (librpl_checked.so, built by build.build(checked=True))
+LIB_PATH = os.path.join(_HERE, "librpl_checked.so" if os.environ.get("RPL_CHECKED") == "1" else "librpl.so")
 
 RPL_OK = 0
 RPL_ERR_TIMEOUT = 6
