@@ -72,3 +72,45 @@ def test_scale_properties_every_pixel(scale):
         n = z.size
         assert abs(dropped.mean() - sen.p_drop) < 5 * math.sqrt(sen.p_drop * (1 - sen.p_drop) / n)
         assert 0.3 < np.mean(z[~dropped] < cam.d_max) < 0.999            # hits and misses both occur
+
+
+@pytest.mark.slow
+def test_many_envs_index_arithmetic(cuda, rpl_lib):
+    """65,536 envs (100,663,296 rays, 786,432 blocks) on the small scene: the 64-bit tile, ring and
+    output indexing stays right across the whole range -- sampled rays from the first and last envs
+    and the middle match the oracle, and the frame matches re-rendering the last envs alone with
+    their env_offset."""
+    torch = cuda
+    E = 65536
+    w = W.config_small(n_steps=1, n_envs=E)
+    sen = W.Sensor(sigma_abs=0.01, p_drop=0.02, max_latency=1, seed=(0x61, 0x62))
+    scene = rpl_lib.Scene.from_workload(w)
+    view = rpl_lib.View(scene, E, w.n_links)
+    view.set_cameras(w.cameras)
+    view.set_sensor(sen)
+    poses = torch.from_numpy(w.poses[0]).cuda()
+    out = view.render(poses, 0).cpu().numpy()
+    view.sync()
+    tail = 1000
+    part = rpl_lib.View(scene, tail, w.n_links)
+    part.set_cameras(w.cameras)
+    part.set_sensor(sen)
+    got_tail = part.render(poses[E - tail:].contiguous(), 0, E - tail).cpu().numpy()
+    part.sync()
+    assert np.array_equal(out[E - tail:], got_tail)
+    rng = np.random.default_rng(65)
+    envs = np.concatenate([np.arange(4), np.arange(E - 4, E), rng.integers(0, E, 8)])
+    rays = []
+    for e in envs:
+        for c, cam in enumerate(w.cameras):
+            for _ in range(8):
+                rays.append([e, c, rng.integers(0, cam.width), rng.integers(0, cam.height)])
+    rays = np.asarray(rays, np.int64)
+    osc = oracle.OracleScene.from_workload(w)
+    ref = osc.render(w.cameras, w.poses, 0, rays, sen, s_first=np.zeros(E, np.int64))
+    offs = w.cam_offsets()
+    cw = np.array([c.width for c in w.cameras])
+    got = out[rays[:, 0], offs[rays[:, 1]] + rays[:, 3] * cw[rays[:, 1]] + rays[:, 2]]
+    dropped = (ref["flags"] & oracle.FLAG_DROPPED) != 0
+    assert np.array_equal(got == np.float32(sen.fill), dropped)
+    compare_depth(got, ref["depth"], ref["flags"], "65536 envs")
