@@ -222,12 +222,22 @@ def cpu_baseline(w, seconds, gpu_step0=None):
     t = time.perf_counter()
     ref = sc.render(w.cameras, w.poses, 0, rays, w.sensor, **extra)
     dt = time.perf_counter() - t
+    # one core, on a small slice of the same sample (about a tenth of the all-core time)
+    one = rays[:max(1, int(n * 0.1 / cores) or 1)]
+    t = time.perf_counter()
+    sc.render(w.cameras, w.poses, 0, one, w.sensor, **dict(extra, threads=1))
+    dt1 = time.perf_counter() - t
     sc.close()
-    per_px = np.array([max(1, c.downsample) ** 2 for c in w.cameras])[rays[:, 1]]
-    n_rays = int(per_px.sum())                       # a downsampled pixel costs f^2 ray casts
-    out = {"value": n_rays / dt / 1e9, "unit": "Grays/s", "cores": cores, "kind": "oracle",
+    per_px = np.array([max(1, c.downsample) ** 2 for c in w.cameras])
+    n_rays = int(per_px[rays[:, 1]].sum())           # a downsampled pixel costs f^2 ray casts
+    n_one = int(per_px[one[:, 1]].sum())
+    rate = n_rays / dt
+    out = {"value": rate / 1e9, "unit": "Grays/s", "cores": cores, "kind": "oracle",
            "sample": "%d output pixels (%d ray casts) drawn uniformly over (env, camera, pixel) of step 0, FP64 "
-                     "brute force over all triangles, %.1f s" % (n, n_rays, dt)}
+                     "brute force over all triangles, %.1f s" % (n, n_rays, dt),
+           "single_core_value": n_one / dt1 / 1e9,
+           "single_core_sample": "%d output pixels of the same sample on one thread, %.1f s" % (len(one), dt1),
+           "full_step_s_extrapolated": w.rays_per_step / rate}
     if gpu_step0 is not None:
         offs = w.cam_offsets()
         cw = np.array([c.out_width for c in w.cameras])
@@ -251,8 +261,9 @@ def run_reference(args):
     w = workload(args, 0)
     n_tot = dt_tot = 0
     cores = os.cpu_count() or 1
+    cb = {}
     for k in range(args.warmup + args.steps):
-        n, dt, cores, _ = cpu_baseline(w, max(1.0, args.cpu_seconds / max(1, args.steps)))
+        n, dt, cores, cb = cpu_baseline(w, max(1.0, args.cpu_seconds / max(1, args.steps)))
         if k >= args.warmup:
             n_tot += n
             dt_tot += dt
@@ -266,7 +277,8 @@ def run_reference(args):
             "frames_per_s": rate / (w.raw_pixels_per_env / len(w.cameras)),
             "e2e": {"value": rate / 1e9, "unit": "Grays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "cpu_baseline": {"value": rate / 1e9, "unit": "Grays/s", "cores": cores, "kind": "oracle",
-                             "sample": sample}}
+                             "sample": sample, "single_core_value": cb.get("single_core_value"),
+                             "full_step_s_extrapolated": w.rays_per_step / rate}}
     print(json.dumps(line), flush=True)
 
 
