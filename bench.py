@@ -205,12 +205,15 @@ def sample_rays(w, n, rng):
     return np.stack([rng.integers(0, w.n_envs, n), c, x, y], 1).astype(np.int64)
 
 
-def cpu_baseline(w, seconds, gpu_step0=None):
+def cpu_baseline(w, seconds, gpu_step0=None, sc=None, single_core=True):
     """The FP64 oracle, as it stands, on a bounded sample of rays of step 0 of the same workload.  When
-    the GPU's step-0 frame is given, the sample also yields the GPU's error against the oracle."""
+    the GPU's step-0 frame is given, the sample also yields the GPU's error against the oracle.  `sc`
+    reuses an oracle scene across calls; single_core adds a one-thread slice of the sample."""
     import oracle
     cores = os.cpu_count() or 1
-    sc = oracle.OracleScene.from_workload(w)
+    own = sc is None
+    if own:
+        sc = oracle.OracleScene.from_workload(w)
     rng = np.random.default_rng(1234)
     extra = dict(per_env_intrinsics=w.per_env_intrinsics, mount_dr=w.mount_delta, rsm_mode=w.rsm_modes,
                  rsm_cols=w.rsm_cols, flags=False, threads=cores)
@@ -222,22 +225,23 @@ def cpu_baseline(w, seconds, gpu_step0=None):
     t = time.perf_counter()
     ref = sc.render(w.cameras, w.poses, 0, rays, w.sensor, **extra)
     dt = time.perf_counter() - t
-    # one core, on a small slice of the same sample (about a tenth of the all-core time)
-    one = rays[:max(1, int(n * 0.1 / cores) or 1)]
-    t = time.perf_counter()
-    sc.render(w.cameras, w.poses, 0, one, w.sensor, **dict(extra, threads=1))
-    dt1 = time.perf_counter() - t
-    sc.close()
     per_px = np.array([max(1, c.downsample) ** 2 for c in w.cameras])
     n_rays = int(per_px[rays[:, 1]].sum())           # a downsampled pixel costs f^2 ray casts
-    n_one = int(per_px[one[:, 1]].sum())
     rate = n_rays / dt
     out = {"value": rate / 1e9, "unit": "Grays/s", "cores": cores, "kind": "oracle",
            "sample": "%d output pixels (%d ray casts) drawn uniformly over (env, camera, pixel) of step 0, FP64 "
                      "brute force over all triangles, %.1f s" % (n, n_rays, dt),
-           "single_core_value": n_one / dt1 / 1e9,
-           "single_core_sample": "%d output pixels of the same sample on one thread, %.1f s" % (len(one), dt1),
            "full_step_s_extrapolated": w.rays_per_step / rate}
+    if single_core:
+        # one core, on a small slice of the same sample (about a tenth of the all-core time)
+        one = rays[:max(1, int(n * 0.1 / cores))]
+        t = time.perf_counter()
+        sc.render(w.cameras, w.poses, 0, one, w.sensor, **dict(extra, threads=1))
+        dt1 = time.perf_counter() - t
+        out["single_core_value"] = int(per_px[one[:, 1]].sum()) / dt1 / 1e9
+        out["single_core_sample"] = "%d output pixels of the same sample on one thread, %.1f s" % (len(one), dt1)
+    if own:
+        sc.close()
     if gpu_step0 is not None:
         offs = w.cam_offsets()
         cw = np.array([c.out_width for c in w.cameras])
@@ -261,12 +265,16 @@ def run_reference(args):
     w = workload(args, 0)
     n_tot = dt_tot = 0
     cores = os.cpu_count() or 1
+    import oracle
+    sc = oracle.OracleScene.from_workload(w)
     cb = {}
     for k in range(args.warmup + args.steps):
-        n, dt, cores, cb = cpu_baseline(w, max(1.0, args.cpu_seconds / max(1, args.steps)))
+        last = k == args.warmup + args.steps - 1
+        n, dt, cores, cb = cpu_baseline(w, max(1.0, args.cpu_seconds / max(1, args.steps)), sc=sc, single_core=last)
         if k >= args.warmup:
             n_tot += n
             dt_tot += dt
+    sc.close()
     rate = n_tot / dt_tot
     sample = "%d ray casts per step for output pixels drawn uniformly over (env, camera, pixel), brute force over all %d triangles" % (
         n_tot // max(1, args.steps), len(w.terrain_tris) + sum(len(t) for t in w.link_tris))
