@@ -449,15 +449,8 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
             if (kCount) ++cnt.nodes;
             float t0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmax);
             float t1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmax);
-            int e0 = n3.x, e1 = n3.y;
-            if (e0 < 0) {
-                if (n3.z == 0) t0 = CUDART_INF_F;
-                else e0 = leaf_ref(e0, n3.z);
-            }
-            if (e1 < 0) {
-                if (n3.w == 0) t1 = CUDART_INF_F;
-                else e1 = leaf_ref(e1, n3.w);
-            }
+            // leaf children arrive encoded and empty ones never hit (device layout, see rpl_api.cpp)
+            const int e0 = n3.x, e1 = n3.y;
             const bool h0 = t0 != CUDART_INF_F, h1 = t1 != CUDART_INF_F;
             if (h0 && h1) {
                 const bool first0 = t0 <= t1;

@@ -119,6 +119,31 @@ rpl_status to_host(const void *src, size_t bytes, int device, std::vector<char> 
     return RPL_OK;
 }
 
+// The binary layout as the kernels read it: a leaf child carries its final reference
+// ~((first << 3) | (count - 1)) and an empty child a zero-size box at 1e30, which no ray with a
+// finite bound meets, so the traversal decodes nothing per child.  (The host layout, which the
+// collapses and rpl_bvh_build_host use, keeps ~first and the count.)
+void encode_for_device(std::vector<BvhNode> &nodes) {
+    for (BvhNode &n : nodes) {
+        if (n.child0 < 0) {
+            if (n.cnt0 == 0) {
+                n.c0lox = n.c0hix = n.c0loy = n.c0hiy = n.c0loz = n.c0hiz = 1e30f;
+                n.child0 = -1;
+            } else {
+                n.child0 = ~((~n.child0 << 3) | (n.cnt0 - 1));
+            }
+        }
+        if (n.child1 < 0) {
+            if (n.cnt1 == 0) {
+                n.c1lox = n.c1hix = n.c1loy = n.c1hiy = n.c1loz = n.c1hiz = 1e30f;
+                n.child1 = -1;
+            } else {
+                n.child1 = ~((~n.child1 << 3) | (n.cnt1 - 1));
+            }
+        }
+    }
+}
+
 void quat_normalise(const float in[4], float out[4]) {
     double n = std::sqrt((double)in[0] * in[0] + (double)in[1] * in[1] + (double)in[2] * in[2] +
                          (double)in[3] * in[3]);
@@ -295,6 +320,7 @@ RPL_API rpl_status rpl_scene_create(const float *verts, int64_t n_verts, const i
             s->t_depth = wide.depth;
         }
         s->t_n_tris = (int64_t)tri_src->size();
+        if (o.bvh_kind == RPL_BVH2) encode_for_device(bvh.nodes);
         cudaError_t e = s->t_nodes.alloc(node_bytes);
         if (e == cudaSuccess) e = s->t_tris.alloc(std::max<size_t>(tri_src->size(), 1) * sizeof(BvhTri));
         if (e == cudaSuccess) e = cudaMemcpy(s->t_nodes.p, node_src, node_bytes, cudaMemcpyHostToDevice);
@@ -365,6 +391,9 @@ static rpl_status freeze(rpl_scene *s) {
             r[4 + a] = b.root_hi[a];
         }
     }
+    // leaf references carry (first triangle << 3) in 31 bits during traversal
+    if (tris.size() >= (size_t)0x0FFFFFFF) return fail(RPL_ERR_CAPACITY, "the link meshes hold too many triangles");
+    encode_for_device(nodes);
     if (nodes.empty()) nodes.push_back(BvhNode{});
     if (tris.empty()) tris.push_back(BvhTri{});
     cudaError_t e = s->l_nodes.alloc(nodes.size() * sizeof(BvhNode));
