@@ -447,7 +447,7 @@ def run_ours(args):
                          % (info["terrain_bytes"] / 1e9)},
         "frames_per_s": frames,
         "env_steps_per_s": world * w.n_envs / (ms_step / 1e3),
-        "gpu_launches": ((3 if graph else 2) + (1 if raw_rays else 0)) * args.steps,
+        "gpu_launches": ((4 if graph else 3) + (1 if raw_rays else 0)) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic_per_launch(rays, args.variant, tuning, bvh_number(args)),
                      "kernel": "render_kernel", "kernel_ms": 1e3 * k_avg_s,

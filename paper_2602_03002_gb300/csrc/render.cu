@@ -77,6 +77,22 @@ __device__ __forceinline__ uint4 sensor_words(uint32_t env, uint32_t cam, uint32
     return philox10(make_uint4(env, cam, pix, (uint32_t)s), seed0 ^ (uint32_t)(s >> 32), seed1);
 }
 
+// Latency word of (env, camera, step): the delay k = (w0 (Lmax + 1)) >> 32 drawn from the word with
+// pixel field 0xFFFFFFFF, the source step s' = max(s - k, first step since reset) stored as s - s' in
+// bits 0..7, and the ring slot s mod span in bits 8..15 (span = Lmax + 1 <= 16), so that the
+// per-pixel sensor code needs no 64-bit division.  0 when latency is off.
+__device__ __forceinline__ uint32_t latency_word(uint32_t env, uint32_t cam, int64_t step, int64_t first,
+                                                 uint32_t span, uint32_t seed0, uint32_t seed1) {
+    if (span <= 1) return 0u;
+    const uint4 wl = sensor_words(env, cam, 0xFFFFFFFFu, step, seed0, seed1);
+    int64_t src = step - (int64_t)__umulhi(wl.x, span);
+    if (src < first) src = first;
+    if (src > step) src = step;
+    int64_t slot = step % (int64_t)span;
+    if (slot < 0) slot += span;
+    return (uint32_t)(step - src) | ((uint32_t)slot << 8);
+}
+
 // Rotation matrix (row-major) of a quaternion (x, y, z, w), normalised in FP32.
 __device__ __forceinline__ void quat_rot(float x, float y, float z, float w, float R[9]) {
     const float inv = 1.0f / sqrtf(x * x + y * y + z * z + w * w);
@@ -115,6 +131,66 @@ __device__ __forceinline__ bool link_world_box(const PrepParams &p, int64_t el, 
 __device__ __forceinline__ bool boxes_overlap(float alx, float ahx, float aly, float ahy, float alz, float ahz,
                                               const float blo[3], const float bhi[3]) {
     return alx <= bhi[0] && blo[0] <= ahx && aly <= bhi[1] && blo[1] <= ahy && alz <= bhi[2] && blo[2] <= ahz;
+}
+
+// The view pyramid of a rectangle of pixels: apex o (the camera origin) and far face at z-depth d_max
+// through the rectangle's corner pixels.  Every ray segment of those pixels lies inside it, for
+// z-depth and for range depth (a range segment of length d_max ends at z-depth
+// d_max / |(r_x, r_y, 1)| <= d_max), since the pixel directions R_c (r_x, r_y, 1) are affine in the
+// pixel coordinates.  Holds the padded AABB, the four side-plane normals oriented inward (towards
+// the mean corner direction, which lies inside the pyramid even when the optical axis does not)
+// and the optical axis for the far plane.
+struct Pyramid {
+    float o[3], N[4][3], axis[3], d_max;
+    float lo[3], hi[3];
+};
+
+// B: far corners o + d_max R_c (r_x, r_y, 1) in ring order around the rectangle.
+__device__ __forceinline__ void make_pyramid(Pyramid &P, const float o[3], const float B[4][3], const float axis[3],
+                                             float d_max) {
+    float mean[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        P.o[a] = o[a];
+        P.axis[a] = axis[a];
+        float lo = fminf(fminf(o[a], fminf(B[0][a], B[1][a])), fminf(B[2][a], B[3][a]));
+        float hi = fmaxf(fmaxf(o[a], fmaxf(B[0][a], B[1][a])), fmaxf(B[2][a], B[3][a]));
+        const float slack = 1e-3f + 1e-5f * fmaxf(fabsf(lo), fabsf(hi));
+        P.lo[a] = lo - slack;
+        P.hi[a] = hi + slack;
+        mean[a] = (B[0][a] - o[a]) + (B[1][a] - o[a]) + (B[2][a] - o[a]) + (B[3][a] - o[a]);
+    }
+    P.d_max = d_max;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const float *a = B[s], *b = B[(s + 1) & 3];
+        const float u[3] = {a[0] - o[0], a[1] - o[1], a[2] - o[2]}, v[3] = {b[0] - o[0], b[1] - o[1], b[2] - o[2]};
+        float n[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+        if (n[0] * mean[0] + n[1] * mean[1] + n[2] * mean[2] < 0.f) {
+            n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2];
+        }
+        P.N[s][0] = n[0]; P.N[s][1] = n[1]; P.N[s][2] = n[2];
+    }
+}
+
+// Conservative test of a world box against the pyramid: false only when the box lies outside the
+// padded AABB, behind a side plane or beyond the far plane by more than 1 mm.  (A degenerate
+// rectangle one pixel wide gives a zero normal, which culls nothing.)
+__device__ __forceinline__ bool pyramid_meets_box(const Pyramid &P, const float lo[3], const float hi[3]) {
+    bool inside = boxes_overlap(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2], P.lo, P.hi);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        // the box corner farthest along the inward normal must not be behind the plane
+        const float *n = P.N[s];
+        const float d = n[0] * ((n[0] >= 0.f ? hi[0] : lo[0]) - P.o[0]) + n[1] * ((n[1] >= 0.f ? hi[1] : lo[1]) - P.o[1]) +
+                        n[2] * ((n[2] >= 0.f ? hi[2] : lo[2]) - P.o[2]);
+        inside &= d >= -1e-3f * sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    }
+    // far plane: the box corner nearest along the optical axis must lie within d_max
+    const float *ax = P.axis;
+    const float zn = ax[0] * ((ax[0] >= 0.f ? lo[0] : hi[0]) - P.o[0]) + ax[1] * ((ax[1] >= 0.f ? lo[1] : hi[1]) - P.o[1]) +
+                     ax[2] * ((ax[2] >= 0.f ? lo[2] : hi[2]) - P.o[2]);
+    return inside && zn <= P.d_max + 1e-3f;
 }
 
 // Deepest binary node below `node` that holds everything inside the AABB [lo, hi]: descend while
@@ -226,35 +302,17 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
     float B[4][3];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float rx = ((k & 1) ? (float)(cam.width - 1) - pcx : -pcx) / fx;
-        const float ry = ((k & 2) ? (float)(cam.height - 1) - pcy : -pcy) / fy;
+        // ring order: (0, 0), (w - 1, 0), (w - 1, h - 1), (0, h - 1)
+        const float rx = ((k == 1 || k == 2) ? (float)(cam.width - 1) - pcx : -pcx) / fx;
+        const float ry = (k >= 2 ? (float)(cam.height - 1) - pcy : -pcy) / fy;
 #pragma unroll
         for (int a = 0; a < 3; ++a) B[k][a] = o[a] + cam.d_max * (Rc[3 * a] * rx + Rc[3 * a + 1] * ry + Rc[3 * a + 2]);
     }
-    float flo[3], fhi[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        flo[a] = fminf(fminf(o[a], fminf(B[0][a], B[1][a])), fminf(B[2][a], B[3][a]));
-        fhi[a] = fmaxf(fmaxf(o[a], fmaxf(B[0][a], B[1][a])), fmaxf(B[2][a], B[3][a]));
-        const float slack = 1e-3f + 1e-5f * fmaxf(fabsf(flo[a]), fabsf(fhi[a]));
-        flo[a] -= slack;
-        fhi[a] += slack;
-    }
+    Pyramid V;
+    const float axis[3] = {Rc[2], Rc[5], Rc[8]};
+    make_pyramid(V, o, B, axis, cam.d_max);
 
-    // 1) links whose world AABB meets the view pyramid (4 side planes through the apex, far plane)
-    float N[4][3];
-    const int ring[4] = {0, 1, 3, 2};
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const float *a = B[ring[s]], *b = B[ring[(s + 1) & 3]];
-        const float u[3] = {a[0] - o[0], a[1] - o[1], a[2] - o[2]}, v[3] = {b[0] - o[0], b[1] - o[1], b[2] - o[2]};
-        float n[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
-        // orient inward: towards the optical axis
-        if (n[0] * Rc[2] + n[1] * Rc[5] + n[2] * Rc[8] < 0.f) {
-            n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2];
-        }
-        N[s][0] = n[0]; N[s][1] = n[1]; N[s][2] = n[2];
-    }
+    // 1) links whose world AABB meets the view pyramid
     uint64_t mask = 0;
     for (int l = 0; l < p.L; ++l) {
         if (p.lroot[l] < 0) continue;
@@ -263,41 +321,20 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
         float R[9], lo[3], hi[3];
         quat_rot(ql[3], ql[4], ql[5], ql[6], R);
         if (!link_world_box(p, el, l, R, lo, hi)) continue;
-        bool inside = true;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            // the box corner farthest along the inward normal must not be behind the plane
-            const float d = N[s][0] * ((N[s][0] >= 0.f ? hi[0] : lo[0]) - o[0]) +
-                            N[s][1] * ((N[s][1] >= 0.f ? hi[1] : lo[1]) - o[1]) +
-                            N[s][2] * ((N[s][2] >= 0.f ? hi[2] : lo[2]) - o[2]);
-            const float len = sqrtf(N[s][0] * N[s][0] + N[s][1] * N[s][1] + N[s][2] * N[s][2]);
-            inside &= d >= -1e-3f * len;
-        }
-        // far plane: the box corner nearest along the optical axis must lie within d_max
-        const float zn = Rc[2] * ((Rc[2] >= 0.f ? lo[0] : hi[0]) - o[0]) + Rc[5] * ((Rc[5] >= 0.f ? lo[1] : hi[1]) - o[1]) +
-                         Rc[8] * ((Rc[8] >= 0.f ? lo[2] : hi[2]) - o[2]);
-        inside &= zn <= cam.d_max + 1e-3f;
-        inside &= boxes_overlap(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2], flo, fhi);
-        if (inside) mask |= 1ull << l;
+        if (pyramid_meets_box(V, lo, hi)) mask |= 1ull << l;
     }
 
     // 2) terrain entry node: descend while exactly one child's box meets the view volume's AABB and
     //    that child is an inner node; nothing in the other subtrees can be hit by this camera's rays
-    const int node = descend_any(p.bvh_kind, p.tnodes, 0, flo, fhi RPL_CK_DESCEND_ARGS(p.n_tnodes));
-    // 3) latency of this (env, camera, step): k = (w0 (Lmax + 1)) >> 32 from the word with pixel field
-    //    0xFFFFFFFF; source step s' = max(s - k, first step since reset); stored as s - s'
-    uint32_t delta = 0;
+    const int node = descend_any(p.bvh_kind, p.tnodes, 0, V.lo, V.hi RPL_CK_DESCEND_ARGS(p.n_tnodes));
+    // 3) latency word of this (env, camera, step)
+    uint32_t lat = 0;
     if (p.span > 1) {
         const int64_t step = p.step_dev ? *p.step_dev : p.step;
-        const uint4 wl = sensor_words(p.env_offset + (uint32_t)e, (uint32_t)c, 0xFFFFFFFFu, step, p.seed0, p.seed1);
-        int64_t src = step - (int64_t)__umulhi(wl.x, p.span);
-        const int64_t first = p.s_first[e];
-        if (src < first) src = first;
-        if (src > step) src = step;
-        delta = (uint32_t)(step - src);
+        lat = latency_word(p.env_offset + (uint32_t)e, (uint32_t)c, step, p.s_first[e], p.span, p.seed0, p.seed1);
     }
     p.cam_xf[5 * j + 4] = make_float4(__uint_as_float((uint32_t)mask), __uint_as_float((uint32_t)(mask >> 32)),
-                                      __int_as_float(node), __uint_as_float(delta));
+                                      __int_as_float(node), __uint_as_float(lat));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -767,28 +804,28 @@ __device__ __forceinline__ bool traverse8(const float4 *__restrict__ nodes, cons
     }
 }
 
-// One warp renders one tile of 32 pixel rays (tile_w x tile_h, tile_w = 2^tile_w_log2) of one
-// (env, camera).  Called once per warp, or in a grid-stride loop by the persistent launch; `warp` is
-// uniform across the warp so the warp-wide reductions below see all 32 lanes.
 // The sensor model and the store of output pixel (x, y) of camera c in env e, whose pre-sensor
-// depth at this step is z: ring-buffer write, latency select (source step = step - delta, drawn by
-// the prep kernel), noise on hits, clip, dropout, side mask (Appendix A.2; Sec. 3.2.4).
+// depth at this step is z: ring-buffer write, latency select (source step = step - delay, both from
+// the latency word `lat` the prep kernel drew), noise on hits, clip, dropout, side mask (Appendix A.2;
+// Sec. 3.2.4).
 __device__ __forceinline__ void finish_pixel(const RenderParams &p, int e, int c, const CamDev &cam, int x, int y,
-                                             float z, int64_t step, uint32_t delta) {
+                                             float z, int64_t step, uint32_t lat) {
     const uint32_t pix = (uint32_t)(y * cam.out_w + x);
     const int64_t col = (int64_t)cam.pix_off + pix;
     const uint32_t ge = p.env_offset + (uint32_t)e;
     int64_t src = step;
     uint4 w = make_uint4(0u, 0u, 0u, 0u);
     if (p.sensor_on) {
-        const int64_t span = p.span;
+        const uint32_t span = p.span;
         if (span > 1) {
-            const int64_t slot = ((step % span) + span) % span;
-            p.ring[((int64_t)e * span + slot) * p.pix_per_env + col] = z;
+            // lat (latency_word): delay in bits 0..7, ring slot of this step in bits 8..15
+            const uint32_t delta = lat & 0xFFu, slot = (lat >> 8) & 0xFFu;
+            const int64_t row = (int64_t)e * span;
+            p.ring[(row + slot) * p.pix_per_env + col] = z;
             src = step - (int64_t)delta;
-            if (src != step) {
-                const int64_t sslot = ((src % span) + span) % span;
-                z = p.ring[((int64_t)e * span + sslot) * p.pix_per_env + col];
+            if (delta != 0u) {
+                const uint32_t sslot = slot >= delta ? slot - delta : slot + span - delta;
+                z = p.ring[(row + sslot) * p.pix_per_env + col];
             }
         }
         w = sensor_words(ge, (uint32_t)c, pix, src, p.seed0, p.seed1);
@@ -822,10 +859,64 @@ __device__ __forceinline__ void finish_pixel(const RenderParams &p, int e, int c
     }
 }
 
-template <bool kCount, int kKind>
+// Env and tile within the env of tile `warp` (32-bit division whenever the index fits).
+__device__ __forceinline__ void split_tile(int64_t warp, int32_t tiles_per_env, int &e, int &r_tile) {
+    if ((uint64_t)warp < 0x100000000ull) {
+        const uint32_t w = (uint32_t)warp, q = w / (uint32_t)tiles_per_env;
+        e = (int)q;
+        r_tile = (int)(w - q * (uint32_t)tiles_per_env);
+    } else {
+        e = (int)(warp / tiles_per_env);
+        r_tile = (int)(warp - (int64_t)e * tiles_per_env);
+    }
+}
+
+// Terrain entry node and link mask of a tile, derived by its warp (when no tile-prep output is
+// given): the AABB of the 32 ray segments from o3 along d3 to tmax, padded for FP32 rounding; the
+// deepest terrain node below the camera's entry node that holds the AABB; and, one link of the
+// camera's mask per lane (links 0..31, then 32..63), the links whose world box meets the AABB.
+template <int kKind>
+__device__ __forceinline__ void tile_reach_in_warp(const RenderParams &p, int e, int lane, const float o3[3],
+                                                   const float d3[3], float tmax, int cam_entry, uint64_t cam_mask,
+                                                   int &entry, uint64_t &link_mask) {
+    float tlo[3], thi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float far = o3[a] + d3[a] * tmax;
+        float lo = fminf(o3[a], far), hi = fmaxf(o3[a], far);
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, s));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, s));
+        }
+        const float slack = 1e-3f + 1e-5f * fmaxf(fabsf(lo), fabsf(hi));
+        tlo[a] = lo - slack;
+        thi[a] = hi + slack;
+    }
+    entry = descend_any(kKind, p.tnodes, cam_entry, tlo, thi RPL_CK_DESCEND_ARGS(p.n_tnodes));
+    link_mask = 0;
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        const int l = lane + 32 * half;
+        bool keep = false;
+        if ((cam_mask >> l) & 1ull) {
+            const int64_t el = (int64_t)e * p.L + l;
+            const float4 blo = __ldg(p.link_box + 2 * el), bhi = __ldg(p.link_box + 2 * el + 1);
+            keep = boxes_overlap(blo.x, bhi.x, blo.y, bhi.y, blo.z, bhi.z, tlo, thi);
+        }
+        link_mask |= (uint64_t)__ballot_sync(0xffffffffu, keep) << (32 * half);
+        if ((cam_mask >> 32) == 0) break;
+    }
+}
+
+// One warp renders one tile of 32 pixel rays (tile_w x tile_h, tile_w = 2^tile_w_log2) of one
+// (env, camera).  Called once per warp, or in a grid-stride loop by the persistent launch; `warp` is
+// uniform across the warp so the warp-wide reductions below see all 32 lanes.  kTileInfo: the tile's
+// entry node and link mask come from p.tile_info (else the warp derives them).
+template <bool kCount, int kKind, bool kTileInfo>
 __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp, int lane, int64_t step) {
-    const int e = (int)(warp / p.tiles_per_env);
-    const int r_tile = (int)(warp - (int64_t)e * p.tiles_per_env);
+    int e, r_tile;
+    split_tile(warp, p.tiles_per_env, e, r_tile);
     int c = 0;
     while (c + 1 < p.C && r_tile >= p.cams[c + 1].tile_off) ++c;
     const CamDev &cam = p.cams[c];
@@ -864,38 +955,21 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
     Ray ray;
     make_ray(ray, base, off, d);
 
-    // The tile's reach: AABB of the 32 ray segments, padded for FP32 rounding.  The terrain walk
-    // starts at the deepest node below the camera's entry node that holds everything the tile can
-    // reach, and only links whose world box meets that AABB are tested.  Uniform across the warp.
-    float tlo[3], thi[3];
-    {
-        const float o3[3] = {base.x + off.x, base.y + off.y, base.z + off.z};
-        const float d3[3] = {d.x, d.y, d.z};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float far = o3[a] + d3[a] * tmax;
-            float lo = fminf(o3[a], far), hi = fmaxf(o3[a], far);
-#pragma unroll
-            for (int s = 16; s > 0; s >>= 1) {
-                lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, s));
-                hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, s));
-            }
-            const float slack = 1e-3f + 1e-5f * fmaxf(fabsf(lo), fabsf(hi));
-            tlo[a] = lo - slack;
-            thi[a] = hi + slack;
-        }
-    }
-    const int entry = descend_any(kKind, p.tnodes, __float_as_int(CV.z), tlo, thi RPL_CK_DESCEND_ARGS(p.n_tnodes));
+    // The tile's terrain entry node and link mask (uniform across the warp): from the tile-prep
+    // kernel, or else derived by the warp itself.
 #ifdef RPL_CHECKED
     uint32_t ck_err = 0;
 #endif
-    uint64_t link_mask = 0;
-#pragma unroll 1
-    for (uint64_t mk = cam_mask; mk; mk &= mk - 1) {
-        const int l = __ffsll((long long)mk) - 1;
-        const int64_t el = (int64_t)e * p.L + l;
-        const float4 blo = __ldg(p.link_box + 2 * el), bhi = __ldg(p.link_box + 2 * el + 1);
-        if (boxes_overlap(blo.x, bhi.x, blo.y, bhi.y, blo.z, bhi.z, tlo, thi)) link_mask |= 1ull << l;
+    int entry;
+    uint64_t link_mask;
+    if (kTileInfo) {
+        const int4 ti = __ldg(p.tile_info + warp);
+        entry = ti.x;
+        link_mask = ((uint64_t)(uint32_t)ti.z << 32) | (uint32_t)ti.y;
+    } else {
+        const float o3[3] = {base.x + off.x, base.y + off.y, base.z + off.z};
+        const float d3[3] = {d.x, d.y, d.z};
+        tile_reach_in_warp<kKind>(p, e, lane, o3, d3, tmax, __float_as_int(CV.z), cam_mask, entry, link_mask);
     }
     if (!active) return;
 
@@ -971,7 +1045,8 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
 // kMinBlocks caps registers so that many blocks of 128 threads stay resident per SM (8 -> 64
 // registers, 10 -> 48, 12 -> 40).  With p.persistent the grid holds only as many blocks as fit on
 // the device at once and each warp walks the tiles with a grid stride; otherwise one warp per tile.
-template <bool kCount, int kKind, int kMinBlocks>
+// kTileInfo = false serves callers that run no tile prep (p.tile_info null).
+template <bool kCount, int kKind, int kMinBlocks, bool kTileInfo = true>
 __global__ void __launch_bounds__(128, kMinBlocks) render_kernel(const __grid_constant__ RenderParams p) {
     const int lane = threadIdx.x & 31;
     const int64_t total = (int64_t)p.E * p.tiles_per_env;
@@ -979,7 +1054,61 @@ __global__ void __launch_bounds__(128, kMinBlocks) render_kernel(const __grid_co
     const int64_t step = p.step_dev ? *p.step_dev : p.step;
 #pragma unroll 1
     for (int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); warp < total; warp += stride)
-        render_tile<kCount, kKind>(p, warp, lane, step);
+        render_tile<kCount, kKind, kTileInfo>(p, warp, lane, step);
+}
+
+// Terrain entry node and link mask of every tile, one thread per tile of 32 rays (the same work done
+// by the tile's warp would occupy 32 lanes): the view pyramid of the tile's pixel rectangle; the
+// deepest terrain node below the camera's entry node that holds the pyramid's AABB; and the links of
+// the camera's mask whose world box meets the pyramid.  The corner directions use the same
+// arithmetic as the render kernel's rays; the 1 mm padding covers their FP32 rounding.
+__global__ void __launch_bounds__(256) tile_prep_kernel(const __grid_constant__ RenderParams p) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)p.E * p.tiles_per_env) return;
+    int e, r_tile;
+    split_tile(i, p.tiles_per_env, e, r_tile);
+    int c = 0;
+    while (c + 1 < p.C && r_tile >= p.cams[c + 1].tile_off) ++c;
+    const CamDev &cam = p.cams[c];
+    const int t = r_tile - cam.tile_off;
+    const int tw = 1 << p.tile_w_log2, th = 32 >> p.tile_w_log2;
+    const int x0 = (t % cam.tiles_x) * tw, y0 = (t / cam.tiles_x) * th;
+    const int x1 = min(x0 + tw, cam.width) - 1, y1 = min(y0 + th, cam.height) - 1;
+    float fx = cam.fx, fy = cam.fy, cx = cam.cx, cy = cam.cy;
+    if (p.intr) {
+        const float4 k = __ldg(reinterpret_cast<const float4 *>(p.intr) + (int64_t)e * p.C + c);
+        fx = k.x; fy = k.y; cx = k.z; cy = k.w;
+    }
+    const float4 *cx4 = p.cam_xf + 5 * ((int64_t)e * p.C + c);
+    const float4 R0 = __ldg(cx4), R1 = __ldg(cx4 + 1), R2 = __ldg(cx4 + 2), OF = __ldg(cx4 + 3);
+    const float4 CV = __ldg(cx4 + 4);
+    const uint64_t cam_mask = ((uint64_t)__float_as_uint(CV.y) << 32) | __float_as_uint(CV.x);
+    const float o[3] = {R0.w + OF.x, R1.w + OF.y, R2.w + OF.z};
+    const float rxa = __fdiv_rn((float)x0 - cx, fx), rxb = __fdiv_rn((float)x1 - cx, fx);
+    const float rya = __fdiv_rn((float)y0 - cy, fy), ryb = __fdiv_rn((float)y1 - cy, fy);
+    float B[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        // ring order: (x0, y0), (x1, y0), (x1, y1), (x0, y1)
+        const float rx = (k == 1 || k == 2) ? rxb : rxa, ry = k >= 2 ? ryb : rya;
+        B[k][0] = o[0] + cam.d_max * (R0.x * rx + R0.y * ry + R0.z);
+        B[k][1] = o[1] + cam.d_max * (R1.x * rx + R1.y * ry + R1.z);
+        B[k][2] = o[2] + cam.d_max * (R2.x * rx + R2.y * ry + R2.z);
+    }
+    Pyramid V;
+    const float axis[3] = {R0.z, R1.z, R2.z};
+    make_pyramid(V, o, B, axis, cam.d_max);
+    const int entry = descend_any(p.bvh_kind, p.tnodes, __float_as_int(CV.z), V.lo, V.hi RPL_CK_DESCEND_ARGS(p.n_tnodes));
+    uint64_t mask = 0;
+#pragma unroll 1
+    for (uint64_t mk = cam_mask; mk; mk &= mk - 1) {
+        const int l = __ffsll((long long)mk) - 1;
+        const int64_t el = (int64_t)e * p.L + l;
+        const float4 blo = __ldg(p.link_box + 2 * el), bhi = __ldg(p.link_box + 2 * el + 1);
+        const float lo[3] = {blo.x, blo.y, blo.z}, hi[3] = {bhi.x, bhi.y, bhi.z};
+        if (pyramid_meets_box(V, lo, hi)) mask |= 1ull << l;
+    }
+    p.tile_info[i] = make_int4(entry, (int)(uint32_t)mask, (int)(uint32_t)(mask >> 32), 0);
 }
 
 // Several render requests (each with its own view, envs, cameras and sensor) in one launch: the
@@ -1001,7 +1130,7 @@ __global__ void __launch_bounds__(128, kMinBlocks)
         }
         const RenderParams &p = reqs[lo];
         const int64_t step = p.step_dev ? *p.step_dev : p.step;
-        render_tile<false, kKind>(p, warp - prefix[lo], lane, step);
+        render_tile<false, kKind, true>(p, warp - prefix[lo], lane, step);
         if (p.done_counter) {
             // per-request completion inside the fused launch: every lane's stores are made visible,
             // then the warp counts its tile off; the warp that finishes the request's last tile
@@ -1054,16 +1183,10 @@ __global__ void __launch_bounds__(256) sensor_kernel(const __grid_constant__ Ren
         const CamDev &cam = p.cams[c];
         const int pix = col - cam.pix_off;
         const int y = pix / cam.out_w, x = pix - y * cam.out_w;
-        uint32_t delta = 0;
-        if (p.span > 1) {
-            const uint4 wl = sensor_words(p.env_offset + (uint32_t)e, (uint32_t)c, 0xFFFFFFFFu, step, p.seed0, p.seed1);
-            int64_t s0 = step - (int64_t)__umulhi(wl.x, p.span);
-            const int64_t first = p.s_first[e];
-            if (s0 < first) s0 = first;
-            if (s0 > step) s0 = step;
-            delta = (uint32_t)(step - s0);
-        }
-        finish_pixel(p, e, c, cam, x, y, src[i], step, delta);
+        const uint32_t lat = p.span > 1 ? latency_word(p.env_offset + (uint32_t)e, (uint32_t)c, step, p.s_first[e],
+                                                       p.span, p.seed0, p.seed1)
+                                        : 0u;
+        finish_pixel(p, e, c, cam, x, y, src[i], step, lat);
     }
 }
 
@@ -1090,7 +1213,9 @@ namespace {
 // The render kernel for one terrain layout; the counting variant runs with 8 blocks per SM.
 template <int kKind>
 void launch_kind(const RenderParams &p, bool count, int min_blocks, unsigned g, cudaStream_t s) {
-    if (count)
+    if (p.tile_info == nullptr)
+        render_kernel<false, kKind, 8, false><<<g, 128, 0, s>>>(p);   // callers without tile prep (no counters)
+    else if (count)
         render_kernel<true, kKind, 8><<<g, 128, 0, s>>>(p);
     else if (min_blocks == 12)
         render_kernel<false, kKind, 12><<<g, 128, 0, s>>>(p);
@@ -1112,6 +1237,14 @@ void launch_multi_kind(const RenderParams *reqs_dev, const int64_t *prefix_dev, 
 }
 
 }  // namespace
+
+cudaError_t launch_tile_prep(const RenderParams &p, cudaStream_t s) {
+    const int64_t n = (int64_t)p.E * p.tiles_per_env;
+    if (n == 0 || p.tile_info == nullptr) return cudaSuccess;
+    (void)cudaGetLastError();
+    tile_prep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
     const int64_t warps = (int64_t)p.E * p.tiles_per_env;

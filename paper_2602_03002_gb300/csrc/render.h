@@ -26,7 +26,8 @@ struct CamDev {
 //   cam_xf   [E*C*5] float4: rows of R_c with the mounting link's origin in .w; the mount offset
 //                            rotated into the world (R_l p_off); then (bits of the 64-bit mask of
 //                            links inside the camera's view volume, low and high word, bits of the
-//                            terrain entry node, bits of the latency delay s - s' of this step)
+//                            terrain entry node, bits of the latency word of this step: the delay
+//                            s - s' in bits 0..7 and the ring slot s mod span in bits 8..15)
 struct PrepParams {
     const float *poses;        // [E, L, 7]
     const float4 *link_root;   // [RPL_MAX_LINKS * 2] link-frame root boxes (lo, hi)
@@ -71,6 +72,9 @@ struct RenderParams {
     const float4 *link_xf;
     const float4 *link_box;
     const float4 *cam_xf;
+    // [E * tiles_per_env] per tile of 32 rays: (terrain entry node, link mask low word, high word, 0),
+    // written by the tile-prep kernel; null makes the render kernel derive them itself
+    int4 *tile_info;
     const float *intr;      // [E, C, 4] per-env (fx, fy, cx, cy) or null
     int32_t E, L, C, tiles_per_env;
     int32_t pix_per_env, depth_kind;
@@ -102,6 +106,9 @@ struct RenderParams {
 };
 
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s);
+// Per-tile terrain entry nodes and link masks into p.tile_info (no-op when it is null).  Runs after
+// launch_prep and before launch_render of the same parameters.
+cudaError_t launch_tile_prep(const RenderParams &p, cudaStream_t s);
 cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s);
 // Averages the raw images of downsampled cameras and applies the sensor model to them (no-op when
 // p.raw_per_env == 0).  Runs after launch_render of the same parameters.

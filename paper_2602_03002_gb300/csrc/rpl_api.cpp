@@ -191,6 +191,9 @@ struct rpl_view {
     // downsampled cameras: raw depths [E, raw_per_env]; camera c's raw image starts at raw_off[c]
     DevBuf raw;
     int64_t raw_per_env = 0;
+    // per-tile terrain entry node and link mask [E, tiles per env] int4, sized for the tile shape
+    // with the most tiles
+    DevBuf tile_info;
     int64_t raw_off[RPL_MAX_CAMERAS] = {};
     DevBuf mount_dr;                 // [E, C, 7] per-env mount perturbation (rpl_cameras_randomize)
     DevBuf rsm_mode;                 // [E] side-mask modes (rpl_side_mask_set)
@@ -618,6 +621,15 @@ RPL_API rpl_status rpl_cameras_set(rpl_view_t v, const rpl_camera *cams, int32_t
     v->gen++;
     cudaError_t e = v->cam_xf.alloc((size_t)v->E * n_cams * 5 * sizeof(float4));
     if (e != cudaSuccess) return cuda_fail(e, "rpl_cameras_set: allocating camera transforms");
+    int64_t max_tiles = 0;
+    for (int lw = 2; lw <= 4; ++lw) {
+        const int tw = 1 << lw, th = 32 / tw;
+        int64_t tiles = 0;
+        for (int c = 0; c < n_cams; ++c) tiles += (int64_t)((cams[c].width + tw - 1) / tw) * ((cams[c].height + th - 1) / th);
+        max_tiles = std::max(max_tiles, tiles);
+    }
+    e = v->tile_info.alloc((size_t)v->E * max_tiles * sizeof(int4));
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_cameras_set: allocating the per-tile entry nodes");
     v->raw_per_env = raw;
     for (int c = 0; c < n_cams; ++c) v->raw_off[c] = raw_off[c];
     if (raw > 0) {
@@ -829,6 +841,7 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
     rp.link_xf = v->link_xf.as<const float4>();
     rp.link_box = v->link_box.as<const float4>();
     rp.cam_xf = v->cam_xf.as<const float4>();
+    rp.tile_info = v->tile_info.as<int4>();
     rp.intr = v->intr.p ? v->intr.as<const float>() : nullptr;
     rp.E = v->E;
     rp.L = v->L;
@@ -877,6 +890,8 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
     if (stt != RPL_OK) return stt;
     cudaError_t e = launch_prep(pp, st);
     if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the prep kernel");
+    e = launch_tile_prep(rp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the tile-prep kernel");
     const int slot = (int)(v->n_timed % rpl_view::kTimingSlots);
     const bool timed = v->timing && !step_dev;   // no event records inside a graph capture
     if (timed) cudaEventRecord(v->ev[2 * slot], st);
@@ -1449,6 +1464,8 @@ rpl_status view_prepare(rpl_view *v, const float *poses_dev, int64_t step, int64
     if (s != RPL_OK) return s;
     cudaError_t e = launch_prep(pp, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the prep kernel");
+    e = launch_tile_prep(*rp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the tile-prep kernel");
     *warps = (int64_t)rp->E * rp->tiles_per_env;
     return RPL_OK;
 }

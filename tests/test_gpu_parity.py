@@ -58,6 +58,27 @@ def test_small_sensor_on(cuda, rpl_lib):
         compare_depth(got, ref["depth"], ref["flags"], "small sensor step %d" % s)
 
 
+@pytest.mark.parametrize("leaf,node_cost", [(1, 0.0), (2, 0.0), (8, 100.0)])
+def test_leaf_sizes(cuda, rpl_lib, leaf, node_cost):
+    """Leaves of 1 to 8 triangles (the range the device node layout encodes) give the oracle's frames.
+
+    A node cost of 100 makes the builder keep leaves as large as allowed, so the 8-triangle case
+    holds leaves with 5 to 8 triangles (checked through the node count)."""
+    w = W.config_small(n_steps=1)
+    scene = rpl_lib.Scene.from_workload(w, max_leaf_size=leaf, sah_node_cost=node_cost)
+    info = scene.info()
+    if leaf == 8:
+        # a binary tree with k leaves has k - 1 nodes: mean leaf size above 5
+        assert info["terrain_nodes"] * 5 < info["terrain_tris"], info
+    else:
+        assert info["terrain_nodes"] * leaf >= info["terrain_tris"] - leaf, info
+    outs, _, _ = _render_seq(cuda, rpl_lib, w, [0], scene=scene)
+    osc = oracle.OracleScene.from_workload(w)
+    rays = oracle.all_rays(w.cameras, w.n_envs)
+    ref = osc.render(w.cameras, w.poses, 0, rays, w.sensor)
+    compare_depth(outs[0], ref["depth"], ref["flags"], "leaf size %d" % leaf)
+
+
 def test_latency_is_a_delayed_raw_frame_bitexact(cuda, rpl_lib):
     """Output of step s with latency k equals the undelayed output of step s' = max(s-k, first)."""
     w = W.config_small(n_steps=8)
@@ -117,6 +138,38 @@ def test_ragged_uneven_cameras_per_env_intrinsics(cuda, rpl_lib):
     for s in range(2):
         ref = osc.render(w.cameras, w.poses, s, rays, w.sensor, per_env_intrinsics=intr)
         compare_depth(outs[s], ref["depth"], ref["flags"], "ragged step %d" % s)
+
+
+@pytest.mark.parametrize("tile,depth_kind", [((4, 8), 0), ((8, 4), 1), ((16, 2), 0)])
+def test_principal_point_outside_the_image(cuda, rpl_lib, tile, depth_kind):
+    """Per-tile view pyramids stay conservative when the optical axis misses the image (principal
+    point above the image, and left of it for one camera, right of it for the other), for every tile
+    shape and both depth kinds.  Moving the principal point up turns the torso cameras towards the
+    legs: about a fifth of the pixels see link meshes (2,391 of 12,288 in the oracle's frames)."""
+    import dataclasses
+    torch = cuda
+    w = W.config_small(n_steps=1)
+    w.cameras = [dataclasses.replace(cam, cx=(-3.0 if c == 0 else cam.width + 2.0), cy=-3.0)
+                 for c, cam in enumerate(w.cameras)]
+    sen = W.Sensor(depth_kind=depth_kind)
+    scene = rpl_lib.Scene.from_workload(w)
+    view = rpl_lib.View(scene, w.n_envs, w.n_links)
+    view.set_cameras(w.cameras)
+    view.set_sensor(sen)
+    rpl_lib.rpl_view_tuning_set(view.h, tile[0], tile[1], 0, 1, 10)
+    poses = torch.from_numpy(w.poses).cuda()
+    got = view.render(poses[0], 0).cpu().numpy().copy()
+    osc = oracle.OracleScene.from_workload(w)
+    rays = oracle.all_rays(w.cameras, w.n_envs)
+    ref = osc.render(w.cameras, w.poses, 0, rays, sen)
+    compare_depth(got, ref["depth"], ref["flags"], "principal point outside, tile %dx%d" % tile)
+    # the links are in view: without their meshes some pixels see further
+    bare = rpl_lib.Scene(w.terrain_verts, w.terrain_tris)
+    bview = rpl_lib.View(bare, w.n_envs, w.n_links)
+    bview.set_cameras(w.cameras)
+    bview.set_sensor(sen)
+    far = bview.render(poses[0], 0).cpu().numpy()
+    assert np.count_nonzero(far.reshape(-1) > got.reshape(-1) + 1e-3) > 1000
 
 
 def test_range_depth_kind(cuda, rpl_lib):
