@@ -173,6 +173,7 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
             rp.ltris = si.ltris;
             rp.link_xf = pp.link_xf;
             rp.link_box = pp.link_box;
+            rp.link_root = si.link_root;
             rp.cam_xf = pp.cam_xf;
             rp.intr = nullptr;
             rp.E = n_envs;

@@ -141,7 +141,7 @@ __device__ __forceinline__ bool boxes_overlap(float alx, float ahx, float aly, f
 // the mean corner direction, which lies inside the pyramid even when the optical axis does not)
 // and the optical axis for the far plane.
 struct Pyramid {
-    float o[3], N[4][3], axis[3], d_max;
+    float o[3], V[4][3], N[4][3], axis[3], d_max;
     float lo[3], hi[3];
 };
 
@@ -152,6 +152,8 @@ __device__ __forceinline__ void make_pyramid(Pyramid &P, const float o[3], const
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         P.o[a] = o[a];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) P.V[k][a] = B[k][a];
         P.axis[a] = axis[a];
         float lo = fminf(fminf(o[a], fminf(B[0][a], B[1][a])), fminf(B[2][a], B[3][a]));
         float hi = fmaxf(fmaxf(o[a], fmaxf(B[0][a], B[1][a])), fmaxf(B[2][a], B[3][a]));
@@ -191,6 +193,46 @@ __device__ __forceinline__ bool pyramid_meets_box(const Pyramid &P, const float 
     const float zn = ax[0] * ((ax[0] >= 0.f ? lo[0] : hi[0]) - P.o[0]) + ax[1] * ((ax[1] >= 0.f ? lo[1] : hi[1]) - P.o[1]) +
                      ax[2] * ((ax[2] >= 0.f ? lo[2] : hi[2]) - P.o[2]);
     return inside && zn <= P.d_max + 1e-3f;
+}
+
+// Conservative separating-axis test of the pyramid against an oriented box: centre c, unit axes
+// A[i] (world), half extents h[i].  The box is kept unless one of the pyramid's four side planes or
+// its far plane, or one of the box's three face axes, separates the two by more than 1 mm.  (The
+// edge-cross-product axes are left out: without them the test can only keep more, never less.)
+__device__ __forceinline__ bool pyramid_meets_obb(const Pyramid &P, const float c[3], const float A[3][3],
+                                                  const float h[3]) {
+    const float co[3] = {c[0] - P.o[0], c[1] - P.o[1], c[2] - P.o[2]};
+    bool inside = true;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        // support of the box along the inward normal must reach the plane
+        const float *n = P.N[s];
+        const float r = h[0] * fabsf(n[0] * A[0][0] + n[1] * A[0][1] + n[2] * A[0][2]) +
+                        h[1] * fabsf(n[0] * A[1][0] + n[1] * A[1][1] + n[2] * A[1][2]) +
+                        h[2] * fabsf(n[0] * A[2][0] + n[1] * A[2][1] + n[2] * A[2][2]);
+        inside &= n[0] * co[0] + n[1] * co[1] + n[2] * co[2] + r >= -1e-3f * sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    }
+    {
+        const float *ax = P.axis;
+        const float r = h[0] * fabsf(ax[0] * A[0][0] + ax[1] * A[0][1] + ax[2] * A[0][2]) +
+                        h[1] * fabsf(ax[0] * A[1][0] + ax[1] * A[1][1] + ax[2] * A[1][2]) +
+                        h[2] * fabsf(ax[0] * A[2][0] + ax[1] * A[2][1] + ax[2] * A[2][2]);
+        inside &= ax[0] * co[0] + ax[1] * co[1] + ax[2] * co[2] - r <= P.d_max + 1e-3f;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        // the pyramid's vertices projected on the box axis must overlap [-h, h] around the centre
+        const float *a = A[i];
+        float lo = -(a[0] * co[0] + a[1] * co[1] + a[2] * co[2]), hi = lo;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float q = a[0] * (P.V[k][0] - c[0]) + a[1] * (P.V[k][1] - c[1]) + a[2] * (P.V[k][2] - c[2]);
+            lo = fminf(lo, q);
+            hi = fmaxf(hi, q);
+        }
+        inside &= lo <= h[i] + 1e-3f && hi >= -h[i] - 1e-3f;
+    }
+    return inside;
 }
 
 // Deepest binary node below `node` that holds everything inside the AABB [lo, hi]: descend while
@@ -1106,7 +1148,19 @@ __global__ void __launch_bounds__(256) tile_prep_kernel(const __grid_constant__ 
         const int64_t el = (int64_t)e * p.L + l;
         const float4 blo = __ldg(p.link_box + 2 * el), bhi = __ldg(p.link_box + 2 * el + 1);
         const float lo[3] = {blo.x, blo.y, blo.z}, hi[3] = {bhi.x, bhi.y, bhi.z};
-        if (pyramid_meets_box(V, lo, hi)) mask |= 1ull << l;
+        if (!pyramid_meets_box(V, lo, hi)) continue;
+        // the link's oriented box: its link-frame root box under the link pose (rows of R^T are the
+        // world directions of the link axes)
+        const float4 X0 = __ldg(p.link_xf + 3 * el), X1 = __ldg(p.link_xf + 3 * el + 1),
+                     X2 = __ldg(p.link_xf + 3 * el + 2);
+        const float4 rl = __ldg(p.link_root + 2 * l), rh = __ldg(p.link_root + 2 * l + 1);
+        const float A[3][3] = {{X0.x, X0.y, X0.z}, {X1.x, X1.y, X1.z}, {X2.x, X2.y, X2.z}};
+        const float cl[3] = {0.5f * (rl.x + rh.x), 0.5f * (rl.y + rh.y), 0.5f * (rl.z + rh.z)};
+        const float h[3] = {0.5f * (rh.x - rl.x), 0.5f * (rh.y - rl.y), 0.5f * (rh.z - rl.z)};
+        const float cw[3] = {A[0][0] * cl[0] + A[1][0] * cl[1] + A[2][0] * cl[2] + X0.w,
+                             A[0][1] * cl[0] + A[1][1] * cl[1] + A[2][1] * cl[2] + X1.w,
+                             A[0][2] * cl[0] + A[1][2] * cl[1] + A[2][2] * cl[2] + X2.w};
+        if (pyramid_meets_obb(V, cw, A, h)) mask |= 1ull << l;
     }
     p.tile_info[i] = make_int4(entry, (int)(uint32_t)mask, (int)(uint32_t)(mask >> 32), 0);
 }

@@ -71,6 +71,7 @@ struct RenderParams {
 #endif
     const float4 *link_xf;
     const float4 *link_box;
+    const float4 *link_root;   // [RPL_MAX_LINKS * 2] link-frame root boxes (lo, hi), for tile prep
     const float4 *cam_xf;
     // [E * tiles_per_env] per tile of 32 rays: (terrain entry node, link mask low word, high word, 0),
     // written by the tile-prep kernel; null makes the render kernel derive them itself

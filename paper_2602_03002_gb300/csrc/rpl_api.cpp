@@ -840,6 +840,7 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
 #endif
     rp.link_xf = v->link_xf.as<const float4>();
     rp.link_box = v->link_box.as<const float4>();
+    rp.link_root = s->l_roots.as<const float4>();
     rp.cam_xf = v->cam_xf.as<const float4>();
     rp.tile_info = v->tile_info.as<int4>();
     rp.intr = v->intr.p ? v->intr.as<const float>() : nullptr;
