@@ -409,8 +409,8 @@ __device__ __forceinline__ void make_ray(Ray &r, float3 base, float3 off, float3
     const int kx = r.kz == 2 ? 0 : r.kz + 1;
     const int ky = kx == 2 ? 0 : kx + 1;
     // the shear only has to be the same for every triangle of this ray (watertightness), not the
-    // correctly rounded quotient, so d_k / d_z is a product with the reciprocal
-    r.Sz = 1.0f / comp(d, r.kz);
+    // correctly rounded quotient: an approximate reciprocal (2 ulp) and products with it
+    r.Sz = __fdividef(1.0f, comp(d, r.kz));
     r.Sx = comp(d, kx) * r.Sz;
     r.Sy = comp(d, ky) * r.Sz;
 }
@@ -980,15 +980,16 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
     const float4 R0 = __ldg(cx4), R1 = __ldg(cx4 + 1), R2 = __ldg(cx4 + 2), OF = __ldg(cx4 + 3);
     const float4 CV = __ldg(cx4 + 4);
     const uint64_t cam_mask = ((uint64_t)__float_as_uint(CV.y) << 32) | __float_as_uint(CV.x);
-    const float rx = __fdiv_rn((float)xs - cx, fx), ry = __fdiv_rn((float)ys - cy, fy);
-    const float inv_n = 1.0f / sqrtf(rx * rx + ry * ry + 1.0f);
+    // fast division and reciprocal square root (2 ulp each): they only move the ray by ~1e-7 rad
+    const float rx = __fdividef((float)xs - cx, fx), ry = __fdividef((float)ys - cy, fy);
+    const float inv_n = rsqrtf(rx * rx + ry * ry + 1.0f);
     const float ux = rx * inv_n, uy = ry * inv_n, uz = inv_n;
     const float3 d = make_float3(R0.x * ux + R0.y * uy + R0.z * uz, R1.x * ux + R1.y * uy + R1.z * uz,
                                  R2.x * ux + R2.y * uy + R2.z * uz);
     const float3 base = make_float3(R0.w, R1.w, R2.w);
     const float3 off = make_float3(OF.x, OF.y, OF.z);
     const float m = p.depth_kind == RPL_DEPTH_Z ? inv_n : 1.0f;
-    float tmax = __fdiv_rn(cam.d_max, m);
+    float tmax = __fdividef(cam.d_max, m);
     bool hit = false;
     bool ok = true;
     Counts cnt_t, cnt_l;
@@ -1126,8 +1127,8 @@ __global__ void __launch_bounds__(256) tile_prep_kernel(const __grid_constant__ 
     const float4 CV = __ldg(cx4 + 4);
     const uint64_t cam_mask = ((uint64_t)__float_as_uint(CV.y) << 32) | __float_as_uint(CV.x);
     const float o[3] = {R0.w + OF.x, R1.w + OF.y, R2.w + OF.z};
-    const float rxa = __fdiv_rn((float)x0 - cx, fx), rxb = __fdiv_rn((float)x1 - cx, fx);
-    const float rya = __fdiv_rn((float)y0 - cy, fy), ryb = __fdiv_rn((float)y1 - cy, fy);
+    const float rxa = __fdividef((float)x0 - cx, fx), rxb = __fdividef((float)x1 - cx, fx);
+    const float rya = __fdividef((float)y0 - cy, fy), ryb = __fdividef((float)y1 - cy, fy);
     float B[4][3];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
