@@ -44,12 +44,18 @@ constexpr uint32_t kErrBounds = 4;
     }
 #define RPL_CK_DESCEND_PARAMS , int64_t ck_nodes
 #define RPL_CK_DESCEND_ARGS(n) , (n)
+#define RPL_CK_PUSH(sp, on_fail)                                                                       \
+    if ((sp) >= kStackDepth) {                                                                       \
+        ck_err |= kErrBounds;                                                                        \
+        on_fail;                                                                                     \
+    }
 #else
 #define RPL_CK_PARAMS
 #define RPL_CK_ARGS(n, t, e)
 #define RPL_CK_NODE(i, on_fail)
 #define RPL_CK_DESCEND_PARAMS
 #define RPL_CK_DESCEND_ARGS(n)
+#define RPL_CK_PUSH(sp, on_fail)
 #endif
 
 // ---------------------------------------------------------------------------------------------
@@ -137,9 +143,9 @@ __device__ __forceinline__ bool boxes_overlap(float alx, float ahx, float aly, f
 // through the rectangle's corner pixels.  Every ray segment of those pixels lies inside it, for
 // z-depth and for range depth (a range segment of length d_max ends at z-depth
 // d_max / |(r_x, r_y, 1)| <= d_max), since the pixel directions R_c (r_x, r_y, 1) are affine in the
-// pixel coordinates.  Holds the padded AABB, the four side-plane normals oriented inward (towards
-// the mean corner direction, which lies inside the pyramid even when the optical axis does not)
-// and the optical axis for the far plane.
+// pixel coordinates.  Holds the padded AABB, the four side planes' unit normals oriented inward
+// (towards the mean corner direction, which lies inside the pyramid even when the optical axis does
+// not) and the optical axis for the far plane.
 struct Pyramid {
     float o[3], V[4][3], N[4][3], axis[3], d_max;
     float lo[3], hi[3];
@@ -168,31 +174,37 @@ __device__ __forceinline__ void make_pyramid(Pyramid &P, const float o[3], const
         const float *a = B[s], *b = B[(s + 1) & 3];
         const float u[3] = {a[0] - o[0], a[1] - o[1], a[2] - o[2]}, v[3] = {b[0] - o[0], b[1] - o[1], b[2] - o[2]};
         float n[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
-        if (n[0] * mean[0] + n[1] * mean[1] + n[2] * mean[2] < 0.f) {
-            n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2];
-        }
-        P.N[s][0] = n[0]; P.N[s][1] = n[1]; P.N[s][2] = n[2];
+        // unit normal, oriented inward (a degenerate side keeps the zero normal)
+        const float len2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+        float inv = len2 > 0.f ? rsqrtf(len2) : 0.f;
+        if (n[0] * mean[0] + n[1] * mean[1] + n[2] * mean[2] < 0.f) inv = -inv;
+        P.N[s][0] = n[0] * inv; P.N[s][1] = n[1] * inv; P.N[s][2] = n[2] * inv;
     }
 }
 
 // Conservative test of a world box against the pyramid: false only when the box lies outside the
 // padded AABB, behind a side plane or beyond the far plane by more than 1 mm.  (A degenerate
 // rectangle one pixel wide gives a zero normal, which culls nothing.)
-__device__ __forceinline__ bool pyramid_meets_box(const Pyramid &P, const float lo[3], const float hi[3]) {
-    bool inside = boxes_overlap(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2], P.lo, P.hi);
+// The plane part of the test below (the box is already known to meet the pyramid's AABB).
+__device__ __forceinline__ bool pyramid_planes_meet_box(const Pyramid &P, const float lo[3], const float hi[3]) {
+    bool inside = true;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
         // the box corner farthest along the inward normal must not be behind the plane
         const float *n = P.N[s];
         const float d = n[0] * ((n[0] >= 0.f ? hi[0] : lo[0]) - P.o[0]) + n[1] * ((n[1] >= 0.f ? hi[1] : lo[1]) - P.o[1]) +
                         n[2] * ((n[2] >= 0.f ? hi[2] : lo[2]) - P.o[2]);
-        inside &= d >= -1e-3f * sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        inside &= d >= -1e-3f;
     }
     // far plane: the box corner nearest along the optical axis must lie within d_max
     const float *ax = P.axis;
     const float zn = ax[0] * ((ax[0] >= 0.f ? lo[0] : hi[0]) - P.o[0]) + ax[1] * ((ax[1] >= 0.f ? lo[1] : hi[1]) - P.o[1]) +
                      ax[2] * ((ax[2] >= 0.f ? lo[2] : hi[2]) - P.o[2]);
     return inside && zn <= P.d_max + 1e-3f;
+}
+
+__device__ __forceinline__ bool pyramid_meets_box(const Pyramid &P, const float lo[3], const float hi[3]) {
+    return boxes_overlap(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2], P.lo, P.hi) && pyramid_planes_meet_box(P, lo, hi);
 }
 
 // Conservative separating-axis test of the pyramid against an oriented box: centre c, unit axes
@@ -210,7 +222,7 @@ __device__ __forceinline__ bool pyramid_meets_obb(const Pyramid &P, const float 
         const float r = h[0] * fabsf(n[0] * A[0][0] + n[1] * A[0][1] + n[2] * A[0][2]) +
                         h[1] * fabsf(n[0] * A[1][0] + n[1] * A[1][1] + n[2] * A[1][2]) +
                         h[2] * fabsf(n[0] * A[2][0] + n[1] * A[2][1] + n[2] * A[2][2]);
-        inside &= n[0] * co[0] + n[1] * co[1] + n[2] * co[2] + r >= -1e-3f * sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        inside &= n[0] * co[0] + n[1] * co[1] + n[2] * co[2] + r >= -1e-3f;
     }
     {
         const float *ax = P.axis;
@@ -256,6 +268,105 @@ __device__ __forceinline__ int descend_binary(const float4 *__restrict__ nodes, 
         node = next;
     }
     return node;
+}
+
+// Descent of the binary layout against a tile's view pyramid: from `node`, step into the one child
+// whose box meets the pyramid while that child is an inner node.  Returns the node where it stops;
+// when it stops because both children meet the pyramid and both are inner nodes, they are returned
+// in ca, cb (else -1).  The pyramid test is conservative, so no ray of the tile reaches a triangle
+// outside the subtree of the returned node.  The plane tests run only where both children meet the
+// pyramid's AABB: where one child alone does, stepping into it is safe whether or not the pyramid
+// itself meets it (if it does not, no ray reaches anything below this node at all).
+// One step of that descent on the fetched node n0..n3: the child to step into, or -1 where the
+// descent stops (then ca, cb receive both children when both meet the pyramid and are inner nodes).
+__device__ __forceinline__ int pyramid_step(const float4 &n0, const float4 &n1, const float4 &n2, const int4 &n3,
+                                            const Pyramid &P, int &ca, int &cb) {
+    // empty children of the device layout sit at 1e30 and meet no pyramid
+    const float lo0[3] = {n0.x, n0.z, n2.x}, hi0[3] = {n0.y, n0.w, n2.y};
+    const float lo1[3] = {n1.x, n1.z, n2.z}, hi1[3] = {n1.y, n1.w, n2.w};
+    bool h0 = boxes_overlap(lo0[0], hi0[0], lo0[1], hi0[1], lo0[2], hi0[2], P.lo, P.hi);
+    bool h1 = boxes_overlap(lo1[0], hi1[0], lo1[1], hi1[1], lo1[2], hi1[2], P.lo, P.hi);
+    if (h0 && h1) {
+        h0 = pyramid_planes_meet_box(P, lo0, hi0);
+        h1 = pyramid_planes_meet_box(P, lo1, hi1);
+    }
+    if (h0 && h1) {
+        if (n3.x >= 0 && n3.y >= 0) {
+            ca = n3.x;
+            cb = n3.y;
+        }
+        return -1;
+    }
+    return h0 ? n3.x : (h1 ? n3.y : -1);
+}
+
+__device__ __forceinline__ int descend_binary_pyramid(const float4 *__restrict__ nodes, int node, const Pyramid &P,
+                                                      int &ca, int &cb RPL_CK_DESCEND_PARAMS) {
+    ca = cb = -1;
+#pragma unroll 1
+    for (int depth = 0; depth < kStackDepth; ++depth) {
+        const float4 *n = nodes + 4 * node;
+        const float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2);
+        const int4 n3 = __ldg(reinterpret_cast<const int4 *>(n + 3));
+        const int next = pyramid_step(n0, n1, n2, n3, P, ca, cb);
+        if (next < 0) break;
+#ifdef RPL_CHECKED
+        if (!in_range(next, ck_nodes)) break;
+#endif
+        node = next;
+    }
+    return node;
+}
+
+// The same descent from two nodes at once (the two children of a node the pyramid splits), so that
+// the two chains of dependent node fetches overlap; a, b become the nodes where each one stops.
+__device__ __forceinline__ void descend_binary_pyramid2(const float4 *__restrict__ nodes, int &a, int &b,
+                                                        const Pyramid &P RPL_CK_DESCEND_PARAMS) {
+    bool go_a = true, go_b = true;
+    int xa, xb;
+#pragma unroll 1
+    for (int depth = 0; depth < kStackDepth && (go_a || go_b); ++depth) {
+        const float4 *na = nodes + 4 * a, *nb = nodes + 4 * b;
+        float4 a0, a1, a2, b0, b1, b2;
+        int4 a3, b3;
+        if (go_a) {
+            a0 = __ldg(na); a1 = __ldg(na + 1); a2 = __ldg(na + 2);
+            a3 = __ldg(reinterpret_cast<const int4 *>(na + 3));
+        }
+        if (go_b) {
+            b0 = __ldg(nb); b1 = __ldg(nb + 1); b2 = __ldg(nb + 2);
+            b3 = __ldg(reinterpret_cast<const int4 *>(nb + 3));
+        }
+        if (go_a) {
+            const int next = pyramid_step(a0, a1, a2, a3, P, xa, xb);
+#ifdef RPL_CHECKED
+            go_a = next >= 0 && in_range(next, ck_nodes);
+#else
+            go_a = next >= 0;
+#endif
+            if (go_a) a = next;
+        }
+        if (go_b) {
+            const int next = pyramid_step(b0, b1, b2, b3, P, xa, xb);
+#ifdef RPL_CHECKED
+            go_b = next >= 0 && in_range(next, ck_nodes);
+#else
+            go_b = next >= 0;
+#endif
+            if (go_b) b = next;
+        }
+    }
+}
+
+// Squared distance from point o to the box [lo, hi].
+__device__ __forceinline__ float box_dist2(const float o[3], const float lo[3], const float hi[3]) {
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float d = fmaxf(fmaxf(lo[a] - o[a], o[a] - hi[a]), 0.f);
+        s += d * d;
+    }
+    return s;
 }
 
 // The same for the eight-wide layout (defined with the wide traversal below).
@@ -492,12 +603,15 @@ __device__ __forceinline__ void leaf(const float4 *__restrict__ tris, int first,
 // scenes hold fewer than 2^28 - 1 triangles and leaves at most 8); kDone marks an exhausted stack.
 constexpr int kDone = INT_MIN;
 
+// The traversal's leaf reference of a four-wide child (whose node stores ~first and the count apart).
 __device__ __forceinline__ int leaf_ref(int child, int count) { return ~((~child << 3) | (count - 1)); }
 
 __device__ __forceinline__ int stack_pop(const int *stack, int &sp) { return sp > 0 ? stack[--sp] : kDone; }
 
-// Closest hit below tmax in one BVH; tmax shrinks to the hit distance.  Returns false when the stack
-// would overflow (never for scenes accepted at build time).
+// Closest hit below tmax in one BVH, searched from node `root` and, when root2 >= 0, then from node
+// root2 (two disjoint subtrees); tmax shrinks to the hit distance.  The stack holds at most one
+// entry per level of the current path plus root2, so it cannot overflow for the scenes accepted at
+// build time (BVH depth < kStackDepth); the bounds-checked build verifies every push.  Returns true.
 //
 // Inner nodes and leaves are handled in two phases (Aila and Laine, "Understanding the Efficiency of
 // Ray Traversal on GPUs", HPG 2009): a lane that meets a leaf postpones it and keeps descending
@@ -510,10 +624,10 @@ __device__ __forceinline__ int stack_pop(const int *stack, int &sp) { return sp 
 // warp's (ray, link) pairs so that link BVHs are traversed with full warps.)
 template <bool kSplit, bool kCount>
 __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const float4 *__restrict__ tris, int root,
-                                         const Ray &r, float &tmax, bool &hit, Counts &cnt RPL_CK_PARAMS) {
+                                         int root2, const Ray &r, float &tmax, bool &hit, Counts &cnt RPL_CK_PARAMS) {
     int stack_node[kStackDepth];
     int sp = 0;
-    bool ok = true;
+    if (root2 >= 0) stack_node[sp++] = root2;
     int cur = root;      // >= 0 inner node, < 0 leaf reference, kDone nothing left
     int pending = 0;     // postponed leaf reference, 0 = none
     auto pop = [&]() -> int { return stack_pop(stack_node, sp); };
@@ -531,22 +645,14 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
             // leaf children arrive encoded and empty ones never hit (device layout, see rpl_api.cpp)
             const int e0 = n3.x, e1 = n3.y;
             const bool h0 = t0 != CUDART_INF_F, h1 = t1 != CUDART_INF_F;
+            // nearer hit child next (child 0 on a tie), the other one pushed; branch-free selects
+            const bool sw = h1 && (!h0 || t1 < t0);
+            const int near = sw ? e1 : e0, far = sw ? e0 : e1;
             if (h0 && h1) {
-                const bool first0 = t0 <= t1;
-                if (sp == kStackDepth) {
-                    ok = false;
-                    cur = kDone;
-                    break;
-                }
-                stack_node[sp++] = first0 ? e1 : e0;
-                cur = first0 ? e0 : e1;
-            } else if (h0) {
-                cur = e0;
-            } else if (h1) {
-                cur = e1;
-            } else {
-                cur = pop();
+                RPL_CK_PUSH(sp, cur = kDone; break)
+                stack_node[sp++] = far;
             }
+            cur = (h0 || h1) ? near : pop();
             if (cur < 0 && cur != kDone && pending == 0) {
                 pending = cur;
                 cur = pop();
@@ -563,7 +669,7 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
                 cur = pop();
             }
         }
-        if (cur == kDone) return ok;
+        if (cur == kDone) return true;
     }
 }
 
@@ -1003,11 +1109,12 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
 #ifdef RPL_CHECKED
     uint32_t ck_err = 0;
 #endif
-    int entry;
+    int entry, entry2 = -1;
     uint64_t link_mask;
     if (kTileInfo) {
         const int4 ti = __ldg(p.tile_info + warp);
         entry = ti.x;
+        entry2 = ti.w;
         link_mask = ((uint64_t)(uint32_t)ti.z << 32) | (uint32_t)ti.y;
     } else {
         const float o3[3] = {base.x + off.x, base.y + off.y, base.z + off.z};
@@ -1040,7 +1147,7 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
                                       X2.x * d.x + X2.y * d.y + X2.z * d.z);
         Ray lr;
         make_ray(lr, ob, make_float3(0.f, 0.f, 0.f), db);
-        ok &= traverse<false, kCount>(p.lnodes, p.ltris, root, lr, tmax, hit, cnt_l RPL_CK_ARGS(p.n_lnodes, p.n_ltris, ck_err));
+        ok &= traverse<false, kCount>(p.lnodes, p.ltris, root, -1, lr, tmax, hit, cnt_l RPL_CK_ARGS(p.n_lnodes, p.n_ltris, ck_err));
     }
     };
     // 2) static terrain, bounded by the closest hit so far
@@ -1051,7 +1158,7 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
         } else if (kKind == RPL_BVH4) {
             ok &= traverse4<kCount>(p.tnodes, p.ttris, entry, ray, tmax, hit, cnt_t RPL_CK_ARGS(p.n_tnodes, p.n_ttris, ck_err));
         } else {
-            ok &= traverse<true, kCount>(p.tnodes, p.ttris, entry, ray, tmax, hit, cnt_t RPL_CK_ARGS(p.n_tnodes, p.n_ttris, ck_err));
+            ok &= traverse<true, kCount>(p.tnodes, p.ttris, entry, entry2, ray, tmax, hit, cnt_t RPL_CK_ARGS(p.n_tnodes, p.n_ttris, ck_err));
         }
     };
     if (p.terrain_first) {
@@ -1105,7 +1212,9 @@ __global__ void __launch_bounds__(128, kMinBlocks) render_kernel(const __grid_co
 // deepest terrain node below the camera's entry node that holds the pyramid's AABB; and the links of
 // the camera's mask whose world box meets the pyramid.  The corner directions use the same
 // arithmetic as the render kernel's rays; the 1 mm padding covers their FP32 rounding.
-__global__ void __launch_bounds__(256) tile_prep_kernel(const __grid_constant__ RenderParams p) {
+// At most 80 registers (3 blocks of 256 per SM): its time is mostly the latency of dependent node
+// fetches, which more resident threads hide (measured: 3 blocks beat 2, 4 and 6).
+__global__ void __launch_bounds__(256, 3) tile_prep_kernel(const __grid_constant__ RenderParams p) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)p.E * p.tiles_per_env) return;
     int e, r_tile;
@@ -1141,7 +1250,26 @@ __global__ void __launch_bounds__(256) tile_prep_kernel(const __grid_constant__ 
     Pyramid V;
     const float axis[3] = {R0.z, R1.z, R2.z};
     make_pyramid(V, o, B, axis, cam.d_max);
-    const int entry = descend_any(p.bvh_kind, p.tnodes, __float_as_int(CV.z), V.lo, V.hi RPL_CK_DESCEND_ARGS(p.n_tnodes));
+    // terrain entry: for the binary layout, the pyramid descent, continued below a node where the
+    // pyramid meets both children (two subtrees, the one nearer the camera first)
+    int entry, entry2 = -1;
+    if (p.bvh_kind == RPL_BVH2) {
+        int ca, cb;
+        entry = descend_binary_pyramid(p.tnodes, __float_as_int(CV.z), V, ca, cb RPL_CK_DESCEND_ARGS(p.n_tnodes));
+        if (ca >= 0) {
+            const float4 *n = p.tnodes + 4 * entry;
+            const float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2);
+            const float lo0[3] = {n0.x, n0.z, n2.x}, hi0[3] = {n0.y, n0.w, n2.y};
+            const float lo1[3] = {n1.x, n1.z, n2.z}, hi1[3] = {n1.y, n1.w, n2.w};
+            int ea = ca, eb = cb;
+            descend_binary_pyramid2(p.tnodes, ea, eb, V RPL_CK_DESCEND_ARGS(p.n_tnodes));
+            const bool a_first = box_dist2(o, lo0, hi0) <= box_dist2(o, lo1, hi1);
+            entry = a_first ? ea : eb;
+            entry2 = a_first ? eb : ea;
+        }
+    } else {
+        entry = descend_any(p.bvh_kind, p.tnodes, __float_as_int(CV.z), V.lo, V.hi RPL_CK_DESCEND_ARGS(p.n_tnodes));
+    }
     uint64_t mask = 0;
 #pragma unroll 1
     for (uint64_t mk = cam_mask; mk; mk &= mk - 1) {
@@ -1163,7 +1291,7 @@ __global__ void __launch_bounds__(256) tile_prep_kernel(const __grid_constant__ 
                              A[0][2] * cl[0] + A[1][2] * cl[1] + A[2][2] * cl[2] + X2.w};
         if (pyramid_meets_obb(V, cw, A, h)) mask |= 1ull << l;
     }
-    p.tile_info[i] = make_int4(entry, (int)(uint32_t)mask, (int)(uint32_t)(mask >> 32), 0);
+    p.tile_info[i] = make_int4(entry, (int)(uint32_t)mask, (int)(uint32_t)(mask >> 32), entry2);
 }
 
 // Several render requests (each with its own view, envs, cameras and sensor) in one launch: the

@@ -73,8 +73,9 @@ struct RenderParams {
     const float4 *link_box;
     const float4 *link_root;   // [RPL_MAX_LINKS * 2] link-frame root boxes (lo, hi), for tile prep
     const float4 *cam_xf;
-    // [E * tiles_per_env] per tile of 32 rays: (terrain entry node, link mask low word, high word, 0),
-    // written by the tile-prep kernel; null makes the render kernel derive them itself
+    // [E * tiles_per_env] per tile of 32 rays: (terrain entry node, link mask low word, high word,
+    // second terrain entry node or -1), written by the tile-prep kernel; null makes the render kernel
+    // derive the entry node and link mask itself
     int4 *tile_info;
     const float *intr;      // [E, C, 4] per-env (fx, fy, cx, cy) or null
     int32_t E, L, C, tiles_per_env;
