@@ -293,8 +293,8 @@ RPL_API rpl_status rpl_view_autotune(rpl_view_t view, const float *link_poses, i
 
 /* Render the next step by replaying a CUDA graph of the whole path (Sec. 3.2.2: the pipeline is
  * captured into a CUDA graph for low-overhead replay).  The first call, and any call after the
- * buffers, env_offset, cameras, sensor or tuning changed, captures prep + render + a step-advance
- * kernel into a graph (on a view-owned stream) and instantiates it; every call then launches it on
+ * buffers, env_offset, cameras, sensor or tuning changed, captures prep + tile prep + render + a
+ * step-advance kernel into a graph (on a view-owned stream) and instantiates it; every call then launches it on
  * `stream`.  The kernels read the step from a view-owned device counter that the graph advances,
  * so replays continue the sensor history: the step rendered is the previous step + 1 (0 for a new
  * view, or the step given to a full rpl_view_reset) and is returned in *step_out (may be NULL).
@@ -332,7 +332,8 @@ typedef struct {
 /* A server for views of `scene`, with a worker thread that, while requests are waiting, admits them
  * in arrival order as stream slots and staging memory free up (at most one request per view on the
  * GPU at a time, since a view's ring buffer and scratch are stateful), fuses the admitted ones into
- * one launch (one prep launch per request, one render launch over the tiles of all of them) on a
+ * one launch (a prep and a tile-prep launch per request, one render launch over the tiles of all
+ * of them) on a
  * free stream, and completes them when that launch's event has passed; batches on different
  * streams overlap on the device.  A request's result is the same as rpl_render of the same view
  * and step alone.  The scene must be frozen (a view created).  Errors: INVALID_ARG, CUDA,
