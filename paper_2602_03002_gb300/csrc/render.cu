@@ -147,7 +147,7 @@ __device__ __forceinline__ bool boxes_overlap(float alx, float ahx, float aly, f
 // (towards the mean corner direction, which lies inside the pyramid even when the optical axis does
 // not) and the optical axis for the far plane.
 struct Pyramid {
-    float o[3], V[4][3], N[4][3], axis[3], d_max;
+    float o[3], V[4][3], N[4][3], tol[4], axis[3], d_max;
     float lo[3], hi[3];
 };
 
@@ -169,23 +169,43 @@ __device__ __forceinline__ void make_pyramid(Pyramid &P, const float o[3], const
         mean[a] = (B[0][a] - o[a]) + (B[1][a] - o[a]) + (B[2][a] - o[a]) + (B[3][a] - o[a]);
     }
     P.d_max = d_max;
+    // reach of the pyramid (its farthest points are the far corners) and size of the apex coordinates
+    float reach = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        reach = fmaxf(reach, sqrtf((B[k][0] - o[0]) * (B[k][0] - o[0]) + (B[k][1] - o[1]) * (B[k][1] - o[1]) +
+                                   (B[k][2] - o[2]) * (B[k][2] - o[2])));
+    const float omag = fmaxf(fmaxf(fabsf(o[0]), fabsf(o[1])), fabsf(o[2]));
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
         const float *a = B[s], *b = B[(s + 1) & 3];
         const float u[3] = {a[0] - o[0], a[1] - o[1], a[2] - o[2]}, v[3] = {b[0] - o[0], b[1] - o[1], b[2] - o[2]};
-        float n[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
-        // unit normal, oriented inward (a degenerate side keeps the zero normal)
-        const float len2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
-        float inv = len2 > 0.f ? rsqrtf(len2) : 0.f;
+        const float n[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+        const float lu = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        const float lv = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const float ln = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        // sine of the angle between the side's two corner rays.  Where they are (nearly) parallel --
+        // a rectangle one pixel wide repeats a corner -- the FP32 cross product is rounding noise
+        // (not zero: the compiler may contract it into FMAs), so the side culls nothing.
+        const float sin_t = lu > 0.f && lv > 0.f ? ln / (lu * lv) : 0.f;
+        if (!(sin_t >= 1e-5f)) {
+            P.N[s][0] = P.N[s][1] = P.N[s][2] = 0.f;
+            P.tol[s] = 0.f;
+            continue;
+        }
+        // unit normal, oriented inward.  Its direction is off by at most delta (radians): the
+        // rounding of the corner directions (relative to the apex coordinates and the reach) and of
+        // the cross product, divided by sin_t; a point of the pyramid then lies up to reach * delta
+        // behind the computed plane, which the tolerance adds to the 1 mm padding.
+        const float delta = (1e-6f + 2e-7f * (omag + reach) / fminf(lu, lv)) / sin_t;
+        P.tol[s] = 1e-3f + reach * delta;
+        float inv = 1.0f / ln;
         if (n[0] * mean[0] + n[1] * mean[1] + n[2] * mean[2] < 0.f) inv = -inv;
         P.N[s][0] = n[0] * inv; P.N[s][1] = n[1] * inv; P.N[s][2] = n[2] * inv;
     }
 }
 
-// Conservative test of a world box against the pyramid: false only when the box lies outside the
-// padded AABB, behind a side plane or beyond the far plane by more than 1 mm.  (A degenerate
-// rectangle one pixel wide gives a zero normal, which culls nothing.)
-// The plane part of the test below (the box is already known to meet the pyramid's AABB).
+// The plane part of pyramid_meets_box (the box is already known to meet the pyramid's AABB).
 __device__ __forceinline__ bool pyramid_planes_meet_box(const Pyramid &P, const float lo[3], const float hi[3]) {
     bool inside = true;
 #pragma unroll
@@ -194,7 +214,7 @@ __device__ __forceinline__ bool pyramid_planes_meet_box(const Pyramid &P, const 
         const float *n = P.N[s];
         const float d = n[0] * ((n[0] >= 0.f ? hi[0] : lo[0]) - P.o[0]) + n[1] * ((n[1] >= 0.f ? hi[1] : lo[1]) - P.o[1]) +
                         n[2] * ((n[2] >= 0.f ? hi[2] : lo[2]) - P.o[2]);
-        inside &= d >= -1e-3f;
+        inside &= d >= -P.tol[s];
     }
     // far plane: the box corner nearest along the optical axis must lie within d_max
     const float *ax = P.axis;
@@ -203,13 +223,17 @@ __device__ __forceinline__ bool pyramid_planes_meet_box(const Pyramid &P, const 
     return inside && zn <= P.d_max + 1e-3f;
 }
 
+// Conservative test of a world box against the pyramid: false only when the box lies outside the
+// padded AABB, behind a side plane by more than that side's tolerance or beyond the far plane by
+// more than 1 mm.
 __device__ __forceinline__ bool pyramid_meets_box(const Pyramid &P, const float lo[3], const float hi[3]) {
     return boxes_overlap(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2], P.lo, P.hi) && pyramid_planes_meet_box(P, lo, hi);
 }
 
 // Conservative separating-axis test of the pyramid against an oriented box: centre c, unit axes
 // A[i] (world), half extents h[i].  The box is kept unless one of the pyramid's four side planes or
-// its far plane, or one of the box's three face axes, separates the two by more than 1 mm.  (The
+// its far plane, or one of the box's three face axes, separates the two by more than the side's
+// tolerance (1 mm for the far plane and the box axes).  (The
 // edge-cross-product axes are left out: without them the test can only keep more, never less.)
 __device__ __forceinline__ bool pyramid_meets_obb(const Pyramid &P, const float c[3], const float A[3][3],
                                                   const float h[3]) {
@@ -222,7 +246,7 @@ __device__ __forceinline__ bool pyramid_meets_obb(const Pyramid &P, const float 
         const float r = h[0] * fabsf(n[0] * A[0][0] + n[1] * A[0][1] + n[2] * A[0][2]) +
                         h[1] * fabsf(n[0] * A[1][0] + n[1] * A[1][1] + n[2] * A[1][2]) +
                         h[2] * fabsf(n[0] * A[2][0] + n[1] * A[2][1] + n[2] * A[2][2]);
-        inside &= n[0] * co[0] + n[1] * co[1] + n[2] * co[2] + r >= -1e-3f;
+        inside &= n[0] * co[0] + n[1] * co[1] + n[2] * co[2] + r >= -P.tol[s];
     }
     {
         const float *ax = P.axis;
@@ -1211,7 +1235,7 @@ __global__ void __launch_bounds__(128, kMinBlocks) render_kernel(const __grid_co
 // by the tile's warp would occupy 32 lanes): the view pyramid of the tile's pixel rectangle; the
 // deepest terrain node below the camera's entry node that holds the pyramid's AABB; and the links of
 // the camera's mask whose world box meets the pyramid.  The corner directions use the same
-// arithmetic as the render kernel's rays; the 1 mm padding covers their FP32 rounding.
+// arithmetic as the render kernel's rays; the padding of each test covers their FP32 rounding.
 // At most 80 registers (3 blocks of 256 per SM): its time is mostly the latency of dependent node
 // fetches, which more resident threads hide (measured: 3 blocks beat 2, 4 and 6).
 __global__ void __launch_bounds__(256, 3) tile_prep_kernel(const __grid_constant__ RenderParams p) {

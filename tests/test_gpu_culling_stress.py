@@ -5,7 +5,8 @@ Each case mounts three cameras on random links with random offsets and orientati
 fields of view from narrow to very wide, sizes from 3 px to 48 px (ragged tiles), principal points
 moved up to 60 % of the image size (often off the image), ranges d_max from 0.4 m to 25 m, per-env
 intrinsics jitter, z-depth or range depth and one of the three tile shapes; the frames are compared
-with the FP64 oracle pixel by pixel.
+with the FP64 oracle pixel by pixel.  (Seed 1 has a tile row one pixel tall: two corners of its
+pyramid coincide, and an FP32 cross product of a corner ray with itself is not exactly zero.)
 """
 import dataclasses
 
@@ -36,7 +37,7 @@ def _random_cameras(rng, seed, n_links):
     return cams
 
 
-@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("seed", list(range(1, 13)))
 def test_random_cameras_match_oracle(cuda, rpl_lib, seed):
     torch = cuda
     rng = np.random.default_rng(seed)
