@@ -4,7 +4,8 @@ subtrees, oriented-box link tests) must never drop geometry a ray can reach.
 Each case mounts three cameras on random links with random offsets and orientations (any roll),
 fields of view from narrow to very wide, sizes from 3 px to 48 px (ragged tiles), principal points
 moved up to 60 % of the image size (often off the image), ranges d_max from 0.4 m to 25 m, per-env
-intrinsics jitter, z-depth or range depth and one of the three tile shapes; the frames are compared
+intrinsics jitter, z-depth or range depth, one of the three tile shapes and, from seed 7 on, one
+camera ray cast at 2x or 3x and block-averaged; the frames are compared
 with the FP64 oracle pixel by pixel.  (Seed 1 has a tile row one pixel tall: two corners of its
 pyramid coincide, and an FP32 cross product of a corner ray with itself is not exactly zero.)
 """
@@ -27,13 +28,15 @@ def _random_cameras(rng, seed, n_links):
     cams = []
     for k in range(3):
         width, height = int(rng.integers(3, 49)), int(rng.integers(2, 41))
+        ds = 2 + seed % 2 if (k == 2 and seed > 6) else 1   # later seeds: one downsampled camera
+        width, height = max(ds, width - width % ds), max(ds, height - height % ds)
         cam = W.pinhole(width, height, float(rng.uniform(20.0, 150.0)), float(rng.uniform(15.0, 120.0)),
                         int(rng.integers(0, n_links)), tuple(rng.uniform(-0.3, 0.3, 3)), 0.0, 0.0,
                         0.05, float(rng.choice([0.4, 1.5, 4.0, 25.0])))
         q = Rotation.random(random_state=1000 * seed + k).as_quat()   # x, y, z, w
         cams.append(dataclasses.replace(cam, offset_quat=tuple(float(v) for v in q),
                                         cx=cam.cx + float(rng.uniform(-0.6, 0.6)) * width,
-                                        cy=cam.cy + float(rng.uniform(-0.6, 0.6)) * height))
+                                        cy=cam.cy + float(rng.uniform(-0.6, 0.6)) * height, downsample=ds))
     return cams
 
 
@@ -63,7 +66,7 @@ def test_random_cameras_match_oracle(cuda, rpl_lib, seed):
     compare_depth(got, ref["depth"], ref["flags"], "random cameras, seed %d" % seed)
     # the frames see something: geometry within range on a good share of the pixels, and link
     # meshes on some of them (without the links those pixels see further; 63 to 2,083 of them)
-    dmax = np.concatenate([np.full(c.width * c.height, c.d_max) for c in w.cameras])
+    dmax = np.concatenate([np.full(c.out_width * c.out_height, c.d_max) for c in w.cameras])
     assert np.mean(ref["depth"].reshape(w.n_envs, -1) < dmax[None, :] - 1e-6) > 0.05
     bare = rpl_lib.Scene(w.terrain_verts, w.terrain_tris)
     bview = rpl_lib.View(bare, w.n_envs, w.n_links)
