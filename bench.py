@@ -13,7 +13,7 @@ Variants (``--variant``):
   serving    Poisson request streams from 4 trainers through the continuous-batching server;
   table1     the paper's Table 1 setting (1024 envs, 240x135, 1 / 2 / 4 cameras): time per render
              and device memory per camera count.
-One step = the whole path over all envs with the next resident pose set: rpl_render (prep + render
+One step = the whole path over all envs with the next resident pose set: rpl_render (prep, tile-prep and render
 kernels), or one graph replay for ``batching``.  The launch shape is chosen by the library's
 autotuner before timing.  Rank 0 prints one JSON line.  ``--impl reference`` times the FP64 CPU
 oracle instead on a bounded sample of the same workload.
