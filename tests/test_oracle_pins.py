@@ -341,6 +341,69 @@ def test_edge_flag_marks_silhouette_rays():
     assert not far["flags"][0] & oracle.FLAG_EDGE and abs(far["depth"][0] - 1.5) < 1e-9
 
 
+def _one_ray_over_plane(height, pitch_deg, rx=0.0, d_max=3.0, depth_kind=0):
+    """One pixel ray of a 1x1 camera at `height` above the plane z = 0, pitched down by pitch_deg;
+    the pixel sits rx (in units of the focal length) to the right of the optical axis."""
+    cam = W.Camera(1, 1, 1.0, 1.0, -rx, 0.0, 0, (0.0, 0.0, 0.0), W.mount_quat(0.0, pitch_deg), 0.1, d_max)
+    out = _render(_plane_mesh(0.0, half=400.0), [EMPTY], [cam], _pose((0.0, 0.0, height))[None, None],
+                  sensor=W.Sensor(depth_kind=depth_kind), flags=True)
+    return int(out["flags"][0]), float(out["raw"][0])
+
+
+@pytest.mark.parametrize("offset,flagged", [(-2e-4, False), (-1.1e-4, False), (-0.9e-4, True), (-5e-5, True),
+                                            (5e-5, True), (0.9e-4, True), (1.1e-4, False), (2e-4, False)])
+def test_far_flag_band(offset, flagged):
+    """FLAG_FAR marks a ray whose unclipped depth lies within 1e-4 m of d_max on either side (there FP32
+    may decide hit or miss differently, and only a hit gets noise).  The depth of the single ray is set
+    by geometry: a camera looking straight down from height d_max + offset at a flat plane."""
+    d_max = 3.0
+    h = float(np.float32(d_max + offset))
+    flags, raw = _one_ray_over_plane(h, 90.0, d_max=d_max)
+    assert abs(min(h, d_max) - raw) < 1e-9                  # the straight-down depth is the height
+    assert bool(flags & oracle.FLAG_FAR) == flagged, (offset, flags)
+
+
+def test_far_flag_not_on_misses_or_far_from_the_band():
+    flags, raw = _one_ray_over_plane(1.0, -30.0)             # looking up: nothing is hit
+    assert raw == 3.0 and not flags & oracle.FLAG_FAR
+    flags, _ = _one_ray_over_plane(1.0, 90.0)                # hit at 1 m, far from d_max
+    assert not flags & oracle.FLAG_FAR
+
+
+def _grazing_u(height, pitch_rad, rx):
+    """The depth change that a 2^-22 rad error of the ray direction causes, from the geometry alone: a
+    ray rx to the right of an optical axis pitched down by p meets the plane at elevation a with
+    sin a = sin p cos phi (tan phi = rx, the right axis is horizontal), after t = height / sin a; the
+    incidence angle to the plane's normal is 90 deg - a, so tan(incidence) = cot a; z-depth = t cos phi,
+    and the offset of the hit along the ray grows with the distance from the camera plus 1 m."""
+    phi = math.atan(rx)
+    a = math.asin(math.sin(pitch_rad) * math.cos(phi))
+    t = height / math.sin(a)
+    return math.cos(phi) * (t + 1.0) * 2.0 ** -22 / math.tan(a)
+
+
+@pytest.mark.parametrize("rx", [0.0, 0.6])
+@pytest.mark.parametrize("ratio", [0.5, 0.95, 1.05, 2.0])
+def test_grazing_flag_threshold(rx, ratio):
+    """FLAG_GRAZING marks a hit whose depth moves by more than 2.5e-5 m (a quarter of the tolerance) when
+    the unit direction is off by 2^-22 rad (FP32 rounding).  The pitch is solved so that this amount,
+    computed from the angle and the distance, is `ratio` times the threshold."""
+    from scipy.optimize import brentq
+    height, thr = 0.5, 2.5e-5
+    p = brentq(lambda p: _grazing_u(height, p, rx) - ratio * thr, math.radians(0.5), math.radians(60.0))
+    flags, raw = _one_ray_over_plane(height, math.degrees(p), rx=rx, d_max=40.0)
+    phi = math.atan(rx)
+    assert abs(raw - height / (math.sin(p) * math.cos(phi)) * math.cos(phi)) < 1e-4   # the plane was hit
+    assert bool(flags & oracle.FLAG_GRAZING) == (ratio > 1.0), (rx, ratio, flags)
+
+
+def test_grazing_flag_not_on_steep_hits_or_misses():
+    flags, _ = _one_ray_over_plane(1.0, 90.0)                # normal incidence
+    assert not flags & oracle.FLAG_GRAZING
+    flags, _ = _one_ray_over_plane(1.0, -10.0, d_max=40.0)   # a miss is never grazing
+    assert not flags & oracle.FLAG_GRAZING
+
+
 # --------------------------------------------------------------------------------------------------
 # sensor model
 # --------------------------------------------------------------------------------------------------
