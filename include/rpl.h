@@ -268,8 +268,12 @@ RPL_API rpl_status rpl_sensor_apply(rpl_view_t view, const float *depth_in, int6
 RPL_API rpl_status rpl_view_host_async(rpl_view_t view, int32_t enable);
 
 /* Launch shape of the render kernel.  tile_w x tile_h = 32 rays per warp (4x8, 8x4 or 16x2
- * pixels of one camera); persistent: launch only as many blocks as fit on the GPU at once and let
- * warps stride over the tiles; terrain_first: query the terrain before the links (Alg. 1 queries
+ * pixels of one camera); persistent: 0 = one warp per tile; 1 = launch only as many blocks as fit
+ * on the GPU at once and let warps stride over the tiles; 2 = as many blocks, the tiles split into
+ * one contiguous queue per SM from which the SM's warps take tiles one at a time (then from the
+ * fullest other queue), so an SM works on neighbouring tiles and no warp waits for the rest of its
+ * block (a view renders on one stream at a time: its queue counters are shared by its renders);
+ * terrain_first: query the terrain before the links (Alg. 1 queries
  * the bodies first; the depth is the same either way); min_blocks: 8 (up to 64 registers per
  * thread), 10 (up to 48) or 12 (up to 40) resident blocks of 128 threads per SM.  The shape never changes the
  * result, only the speed.  Default: 8x4, not persistent, links first, 8. */
@@ -284,7 +288,7 @@ RPL_API rpl_status rpl_view_tuning_set(rpl_view_t view, const rpl_tuning *tuning
 RPL_API rpl_status rpl_view_tuning_get(rpl_view_t view, rpl_tuning *tuning);
 
 /* Autotuner: renders `step` (same step rules as rpl_render; device buffers only) `reps` times
- * with each of the 36 launch shapes (tile 8x4 / 4x8 / 16x2, persistent or not, links or terrain
+ * with each of the 54 launch shapes (tile 8x4 / 4x8 / 16x2, persistent 0 / 1 / 2, links or terrain
  * first, 8, 10 or 12 blocks per SM), times them with CUDA events on `stream`, keeps the fastest on the
  * view and returns it with its mean time per render.  Synchronises; for setup, not the hot loop. */
 RPL_API rpl_status rpl_view_autotune(rpl_view_t view, const float *link_poses, int64_t step,
@@ -420,26 +424,39 @@ RPL_API void rpl_view_destroy(rpl_view_t view);
  * acceptable.  The per-call scratch (per-env link transforms and boxes, per-env camera poses) lives
  * in one fixed __device__ array of RPL_STATIC_SCRATCH_BYTES inside the library, which every GPU
  * that loads the library keeps until the process exits; a call needs
- * 80 * n_envs * (n_links + n_cams) + 16 bytes of it and returns CAPACITY when that exceeds the
- * array (about 3,270 envs with 30 links and 2 cameras).
+ * 80 * n_envs * (n_links + n_cams) bytes of it and returns CAPACITY when that exceeds the array
+ * (about 3,270 envs with 30 links and 2 cameras).
  *   scene       a frozen scene (rpl_view_create has been called on it once), read only
  *   cams        host array of n_cams cameras (1..RPL_MAX_CAMERAS), as for rpl_cameras_set
- *   link_poses  device, [n_envs, n_links, 7] float32
+ *   link_poses  device, [n_envs, n_links, 7] float32, 4-byte aligned
  *   sensor      NULL (clip only) or a sensor with max_latency == 0: noise, clip and dropout are
  *               applied, keyed by (env_offset + env, camera, pixel, step); latency needs a view
- *   depth_out   device, n_envs * (sum of camera pixels) float32, cameras packed per env
+ *   depth_out   device, n_envs * (sum of camera pixels) float32, cameras packed per env, 4-byte
+ *               aligned
  *   stream      cudaStream_t (NULL = legacy default stream)
- * The first call on a device looks up the device address of the array (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  Every call shares the
- * array and it keeps the last call's contents: each call rewrites all of it that it reads, and
- * clears its error word, but calls whose work overlaps on the GPU (other streams, other threads)
- * race on it and must be serialised by the caller.  The call only enqueues work.
+ * The first call on a device looks up the device addresses of the array and of a fixed error word
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream capture.
+ * Every call shares the array and it keeps the last call's contents: each call rewrites all of it
+ * that it reads, but calls whose work overlaps on the GPU (other streams, other threads) race on it
+ * and must be serialised by the caller.  The call only enqueues work.  A fault the kernels detect
+ * (traversal stack overflow; index out of range in the bounds-checked build) is not returned by
+ * this call: it is OR-ed into the fixed error word, which keeps it until rpl_static_scratch_status
+ * reports it.
  * Errors: INVALID_ARG (unfrozen scene, bad counts, cameras or sensor, max_latency != 0, a camera
- * with downsample > 1, whose raw image needs a view's buffer), CAPACITY, CUDA. */
+ * with downsample > 1, whose raw image needs a view's buffer, unaligned buffers), CAPACITY (scratch
+ * beyond the array, 2^31 or more pixels per env), CUDA. */
 RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const rpl_camera *cams, int32_t n_cams,
                                              int32_t n_envs, int32_t n_links, const float *link_poses,
                                              const rpl_sensor_params *sensor, int64_t step,
                                              int64_t env_offset, float *depth_out, void *stream);
+
+/* Reports the kernel-detected faults of rpl_render_static_scratch calls on the scene's device: waits
+ * for `stream` (so give the stream the renders ran on, or synchronise first), reads the fixed error
+ * word, clears it and returns DEVICE_FAULT when it was set (bit 1: traversal stack overflow, bit 4:
+ * node or triangle index out of range, bounds-checked build only), else OK.  The word collects the
+ * faults of every call since the last query.  Like the render call it allocates nothing.
+ * Errors: INVALID_ARG (unfrozen scene), CUDA, DEVICE_FAULT. */
+RPL_API rpl_status rpl_static_scratch_status(rpl_scene_t scene, void *stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 RPL_API const char *rpl_last_error(void);

@@ -8,6 +8,10 @@
 // and output and keeps its scratch in one fixed device array below, so the call itself allocates
 // nothing.  It renders the depth of Algorithm 1 with the stateless part of the sensor model
 // (noise, clip, dropout; no latency, which needs the per-view ring buffer).
+//
+// Kernel-detected errors (a traversal stack overflow; an index out of range in the bounds-checked
+// build) go to a second fixed word, g_static_err, which no render call clears: they stay recorded
+// until rpl_static_scratch_status reads and clears them.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -23,23 +27,33 @@ namespace rpl {
 namespace {
 
 // Fixed scratch shared by every call, on every GPU that loads the library, until the process exits.
-// Layout per call: link_xf [E*L*3 float4], link_box [E*L*2 float4], cam_xf [E*C*5 float4], then
-// one int32 error word (rounded up to 16 bytes).
+// Layout per call: link_xf [E*L*3 float4], link_box [E*L*2 float4], cam_xf [E*C*5 float4].
 static __device__ __align__(256) unsigned char g_scratch[RPL_STATIC_SCRATCH_BYTES];
+// Error bits OR-ed by the render kernels of every call on this device (1: traversal stack
+// overflow, 4: index out of range in the bounds-checked build), until read by the status query.
+static __device__ int32_t g_static_err;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};   // device address of g_scratch per device, set on first use
+struct Addrs {
+    void *scratch = nullptr;   // device address of g_scratch on this device
+    int32_t *err = nullptr;    // device address of g_static_err on this device
+};
+Addrs g_addr[kMaxDevices];     // set on first use of each device
 
-// Looks up the device address of g_scratch for the current device `dev` (once per device).  The
-// host-side name of the array is only a stand-in and must never be passed to a kernel.
-cudaError_t scratch_address(int dev, void **out) {
+// Looks up the device addresses of g_scratch and g_static_err for the current device `dev` (once per
+// device).  The host-side names of these variables are only stand-ins and must never be passed to a
+// kernel.
+cudaError_t fixed_addresses(int dev, Addrs *out) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
+    if (!g_addr[dev].scratch) {
+        void *p = nullptr, *q = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
+        e = cudaGetSymbolAddress(&q, g_static_err);
+        if (e != cudaSuccess) return e;
+        g_addr[dev].scratch = p;
+        g_addr[dev].err = static_cast<int32_t *>(q);
     }
     *out = g_addr[dev];
     return cudaSuccess;
@@ -62,6 +76,8 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
         return set_error(RPL_ERR_INVALID_ARG, "rpl_render_static_scratch: bad camera/env/link count");
     if (n_envs > 0 && (!link_poses || !depth_out))
         return set_error(RPL_ERR_INVALID_ARG, "rpl_render_static_scratch: NULL poses or output");
+    if (((uintptr_t)link_poses & 3) || ((uintptr_t)depth_out & 3))
+        return set_error(RPL_ERR_INVALID_ARG, "rpl_render_static_scratch: poses and output must be 4-byte aligned");
     if (env_offset < 0 || env_offset + (int64_t)n_envs > ((int64_t)1 << 32))
         return set_error(RPL_ERR_INVALID_ARG, "rpl_render_static_scratch: env_offset + n_envs beyond 2^32");
     rpl_sensor_params sp{};
@@ -70,6 +86,7 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
         return set_error(RPL_ERR_INVALID_ARG, "rpl_render_static_scratch: latency needs a view's ring buffer "
                                               "(max_latency must be 0)");
     if (!(sp.p_drop >= 0.f && sp.p_drop <= 1.f) || !(sp.sigma_abs >= 0.f) || !(sp.sigma_rel >= 0.f) ||
+        !std::isfinite(sp.sigma_abs) || !std::isfinite(sp.sigma_rel) || !std::isfinite(sp.fill) ||
         (sp.depth_kind != RPL_DEPTH_Z && sp.depth_kind != RPL_DEPTH_RANGE))
         return set_error(RPL_ERR_INVALID_ARG, "rpl_render_static_scratch: bad sensor parameters");
 
@@ -77,8 +94,7 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
     const size_t EL = (size_t)n_envs * n_links, EC = (size_t)n_envs * n_cams;
     const size_t off_box = EL * 3 * sizeof(float4);
     const size_t off_cam = off_box + EL * 2 * sizeof(float4);
-    const size_t off_err = off_cam + EC * 5 * sizeof(float4);
-    const size_t need = off_err + 16;
+    const size_t need = off_cam + EC * 5 * sizeof(float4);
     if (need > (size_t)RPL_STATIC_SCRATCH_BYTES) {
         char msg[256];
         snprintf(msg, sizeof msg, "rpl_render_static_scratch: needs %zu bytes of scratch, the fixed array holds %d "
@@ -91,10 +107,8 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
     int64_t pix = 0;
     for (int c = 0; c < n_cams; ++c) {
         const rpl_camera &k = cams[c];
-        if (k.width <= 0 || k.height <= 0 || k.width > 16384 || k.height > 16384 || !(k.fx != 0.f) ||
-            !(k.fy != 0.f) || k.mount_link < 0 || k.mount_link >= n_links || !(k.d_min <= k.d_max) ||
-            !(k.d_max > 0.f))
-            return set_error(RPL_ERR_INVALID_ARG, "rpl_render_static_scratch: bad camera");
+        const rpl_status cst = check_camera(k, c, n_links, "rpl_render_static_scratch");
+        if (cst != RPL_OK) return cst;
         if (k.downsample > 1)
             return set_error(RPL_ERR_INVALID_ARG, "rpl_render_static_scratch: a downsampled camera needs a view's "
                                                   "raw-depth buffer");
@@ -123,6 +137,8 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
         for (int a = 0; a < 4; ++a) d.off_quat[a] = n > 0 ? (float)(k.offset_quat_xyzw[a] / n) : (a == 3 ? 1.f : 0.f);
         tiles += ((k.width + 7) / 8) * ((k.height + 3) / 4);
         pix += (int64_t)k.width * k.height;
+        if (pix >= (int64_t)1 << 31)   // pixel offsets inside an env are 32-bit in the kernels
+            return set_error(RPL_ERR_CAPACITY, "rpl_render_static_scratch: 2^31 or more pixels per env");
     }
     if (n_envs == 0) return RPL_OK;
 
@@ -131,11 +147,10 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
     if (si.device < 0 || si.device >= kMaxDevices || cudaSetDevice(si.device) != cudaSuccess)
         return set_error(RPL_ERR_CUDA, "rpl_render_static_scratch: cannot select the scene's device");
     rpl_status st = RPL_OK;
-    void *base = nullptr;
-    cudaError_t e = scratch_address(si.device, &base);
+    Addrs ad;
+    cudaError_t e = fixed_addresses(si.device, &ad);
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    unsigned char *sb = static_cast<unsigned char *>(base);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sb + off_err, 0, sizeof(int32_t), cs);   // error word starts at 0
+    unsigned char *sb = static_cast<unsigned char *>(ad.scratch);
     if (e != cudaSuccess) {
         st = set_error(RPL_ERR_CUDA, cudaGetErrorString(e));
     } else {
@@ -198,7 +213,7 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
             rp.ring = nullptr;
             rp.s_first = nullptr;
             rp.out = depth_out;
-            rp.err = reinterpret_cast<int32_t *>(sb + off_err);
+            rp.err = ad.err;
             rp.counters = nullptr;
             rp.tile_w_log2 = 3;   // 8x4 tiles, as counted above
             rp.min_blocks = 8;
@@ -208,4 +223,34 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
     }
     if (prev >= 0) cudaSetDevice(prev);
     return st;
+}
+
+extern "C" RPL_API rpl_status rpl_static_scratch_status(rpl_scene_t scene, void *stream) {
+    SceneInputs si;
+    if (!scene_inputs(scene, &si))
+        return set_error(RPL_ERR_INVALID_ARG, "rpl_static_scratch_status: scene is NULL or not frozen");
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (si.device < 0 || si.device >= kMaxDevices || cudaSetDevice(si.device) != cudaSuccess)
+        return set_error(RPL_ERR_CUDA, "rpl_static_scratch_status: cannot select the scene's device");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    Addrs ad;
+    int32_t word = 0;
+    static const int32_t zero = 0;
+    cudaError_t e = fixed_addresses(si.device, &ad);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&word, ad.err, sizeof word, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e == cudaSuccess && word != 0) {
+        e = cudaMemcpyAsync(ad.err, &zero, sizeof zero, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    if (e != cudaSuccess) return set_error(RPL_ERR_CUDA, cudaGetErrorString(e));
+    if (word != 0) {
+        char msg[200];
+        snprintf(msg, sizeof msg, "rpl_render_static_scratch: a render kernel recorded error 0x%x (1: traversal "
+                 "stack overflow, 4: node or triangle index out of range)", word);
+        return set_error(RPL_ERR_DEVICE_FAULT, msg);
+    }
+    return RPL_OK;
 }

@@ -412,6 +412,8 @@ __device__ __forceinline__ int descend_any(int kind, const float4 *__restrict__ 
 
 __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepParams p) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p.queues)   // the render kernel's tile queues start empty
+        for (int64_t k = i; k < p.n_queues; k += (int64_t)gridDim.x * blockDim.x) p.queues[k] = 0ull;
     const int64_t n_link = (int64_t)p.E * p.L;
     if (i < n_link) {
         const int l = (int)(i % p.L);
@@ -1219,13 +1221,74 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
 // kMinBlocks caps registers so that many blocks of 128 threads stay resident per SM (8 -> 64
 // registers, 10 -> 48, 12 -> 40).  With p.persistent the grid holds only as many blocks as fit on
 // the device at once and each warp walks the tiles with a grid stride; otherwise one warp per tile.
+// kQueued (p.queues set, same grid as persistent): warps take tiles from per-SM queues instead.
 // kTileInfo = false serves callers that run no tile prep (p.tile_info null).
-template <bool kCount, int kKind, int kMinBlocks, bool kTileInfo = true>
+// First tile of queue q when `total` tiles are split into nq contiguous queues (the first total mod
+// nq queues hold one tile more).
+__device__ __forceinline__ int64_t queue_begin(int64_t total, int q, int nq) {
+    const int64_t base = total / nq, rem = total - base * nq;
+    return base * q + min((int64_t)q, rem);
+}
+
+// Per-SM scheduling (p.queues set): the tiles are split into p.n_queues contiguous queues, one per
+// SM.  A warp takes the next tile of its SM's queue (one atomic per tile), so the SM's warps work on
+// neighbouring tiles of the same images, whose terrain nodes they share in L1; a warp whose block
+// siblings are still busy does not idle, since it takes tiles by itself.  When the SM's queue is
+// empty the warp moves to the queue with the most tiles left, until every queue is empty.  Each
+// warp that finds its queue empty reads every counter (bypassing L1), so it ends only when all
+// queues were seen empty.
+template <bool kCount, int kKind, bool kTileInfo>
+__device__ __forceinline__ void render_queued(const RenderParams &p, int lane, int64_t total, int64_t step) {
+    const int nq = p.n_queues;
+    uint32_t smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    int q = (int)(smid % (uint32_t)nq);
+#pragma unroll 1
+    for (;;) {
+        unsigned long long k = 0ull;
+        if (lane == 0) k = atomicAdd(p.queues + q, 1ull);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        const int64_t b = queue_begin(total, q, nq), size = queue_begin(total, q + 1, nq) - b;
+        if (k < (unsigned long long)size) {
+            render_tile<kCount, kKind, kTileInfo>(p, b + (int64_t)k, lane, step);
+            continue;
+        }
+        // this queue is empty: the queue with the most tiles left (warp-wide argmax)
+        int64_t best = 0;
+        int best_q = -1;
+        for (int j = lane; j < nq; j += 32) {
+            const int64_t sz = queue_begin(total, j + 1, nq) - queue_begin(total, j, nq);
+            const unsigned long long taken = __ldcg(p.queues + j);
+            const int64_t left = taken < (unsigned long long)sz ? sz - (int64_t)taken : 0;
+            if (left > best) {
+                best = left;
+                best_q = j;
+            }
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            const int64_t ob = __shfl_xor_sync(0xffffffffu, best, s);
+            const int oq = __shfl_xor_sync(0xffffffffu, best_q, s);
+            if (ob > best || (ob == best && oq > best_q)) {
+                best = ob;
+                best_q = oq;
+            }
+        }
+        if (best <= 0) return;
+        q = best_q;
+    }
+}
+
+template <bool kCount, int kKind, int kMinBlocks, bool kTileInfo = true, bool kQueued = false>
 __global__ void __launch_bounds__(128, kMinBlocks) render_kernel(const __grid_constant__ RenderParams p) {
     const int lane = threadIdx.x & 31;
     const int64_t total = (int64_t)p.E * p.tiles_per_env;
-    const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t step = p.step_dev ? *p.step_dev : p.step;
+    if (kQueued) {
+        render_queued<kCount, kKind, kTileInfo>(p, lane, total, step);
+        return;
+    }
+    const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 5);
 #pragma unroll 1
     for (int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); warp < total; warp += stride)
         render_tile<kCount, kKind, kTileInfo>(p, warp, lane, step);
@@ -1424,6 +1487,12 @@ void launch_kind(const RenderParams &p, bool count, int min_blocks, unsigned g, 
         render_kernel<false, kKind, 8, false><<<g, 128, 0, s>>>(p);   // callers without tile prep (no counters)
     else if (count)
         render_kernel<true, kKind, 8><<<g, 128, 0, s>>>(p);
+    else if (p.queues && min_blocks == 12)
+        render_kernel<false, kKind, 12, true, true><<<g, 128, 0, s>>>(p);
+    else if (p.queues && min_blocks == 10)
+        render_kernel<false, kKind, 10, true, true><<<g, 128, 0, s>>>(p);
+    else if (p.queues)
+        render_kernel<false, kKind, 8, true, true><<<g, 128, 0, s>>>(p);
     else if (min_blocks == 12)
         render_kernel<false, kKind, 12><<<g, 128, 0, s>>>(p);
     else if (min_blocks == 10)
@@ -1458,7 +1527,7 @@ cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
     if (warps == 0) return cudaSuccess;
     const int min_blocks = p.min_blocks == 12 ? 12 : (p.min_blocks == 10 ? 10 : 8);
     int64_t blocks = (warps + 3) / 4;
-    if (p.persistent) {
+    if (p.persistent || (p.queues && p.tile_info && !count)) {
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
                                                        cudaSuccess && sms > 0)

@@ -49,12 +49,19 @@ struct PrepParams {
     const int64_t *step_dev;   // when set, the step is read from device memory (graph replays)
     const int64_t *s_first;
     uint32_t env_offset, span, seed0, seed1;
+    // tile queues of the render kernel's per-SM scheduling (Tuning::persistent == 2), zeroed here;
+    // null otherwise
+    unsigned long long *queues;
+    int32_t n_queues;
 };
 
 // Launch shape of the render kernel (chosen by the autotuner or set by the caller).
 struct Tuning {
     int32_t tile_w_log2;     // tile of 32 rays: width 2^tile_w_log2 (2..4: 4x8, 8x4, 16x2)
-    int32_t persistent;      // grid of resident blocks only, warps stride over the tiles
+    int32_t persistent;      // 0: one warp per tile; 1: grid of resident blocks only, warps stride
+                             // over the tiles; 2: grid of resident blocks, tiles split into one
+                             // contiguous queue per SM, warps take tiles from their SM's queue and
+                             // then from the fullest other queue
     int32_t terrain_first;   // query the terrain before the links
     int32_t min_blocks;      // 8 (64 registers) or 12 (40 registers) blocks of 128 per SM
 };
@@ -101,6 +108,10 @@ struct RenderParams {
     void *out;                      // [E, pix_per_env] of out_dtype
     int32_t *err;                   // error word (1: traversal stack overflow, 4: index out of range)
     unsigned long long *counters;   // rpl_counters fields, or null
+    // per-SM tile queues (persistent == 2): n_queues counters of tiles taken, zeroed by the prep
+    // kernel; the tiles are split into n_queues contiguous queues of near-equal size; null otherwise
+    unsigned long long *queues;
+    int32_t n_queues;
     // fused launches only (render_multi_kernel): tiles of this request still running, and a word in
     // host-mapped memory set to 1 when the last of them has stored its pixels; null when unused
     int32_t *done_counter;

@@ -194,6 +194,9 @@ struct rpl_view {
     // per-tile terrain entry node and link mask [E, tiles per env] int4, sized for the tile shape
     // with the most tiles
     DevBuf tile_info;
+    // per-SM tile queues of the render kernel (launch shape persistent == 2): one counter per SM
+    DevBuf queues;
+    int32_t n_queues = 0;
     int64_t raw_off[RPL_MAX_CAMERAS] = {};
     DevBuf mount_dr;                 // [E, C, 7] per-env mount perturbation (rpl_cameras_randomize)
     DevBuf rsm_mode;                 // [E] side-mask modes (rpl_side_mask_set)
@@ -555,6 +558,11 @@ RPL_API rpl_status rpl_view_create(rpl_scene_t s, int32_t n_envs, int32_t n_link
         e = cudaHostGetDevicePointer((void **)&v->err_dev, v->err_host, 0);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v->n_queues, cudaDevAttrMultiProcessorCount, s->device);
+    if (e == cudaSuccess) {
+        v->n_queues = std::max(1, v->n_queues);
+        e = v->queues.alloc((size_t)v->n_queues * sizeof(unsigned long long));
+    }
     if (e != cudaSuccess) {
         if (v->err_host) cudaFreeHost(v->err_host);
         if (v->done) cudaEventDestroy(v->done);
@@ -587,19 +595,9 @@ RPL_API rpl_status rpl_cameras_set(rpl_view_t v, const rpl_camera *cams, int32_t
     int32_t toff = 0;
     for (int c = 0; c < n_cams; ++c) {
         const rpl_camera &k = cams[c];
-        if (k.width <= 0 || k.height <= 0 || k.width > 16384 || k.height > 16384)
-            return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: camera %d size %dx%d", c, k.width, k.height);
+        const rpl_status cst = check_camera(k, c, v->L, "rpl_cameras_set");
+        if (cst != RPL_OK) return cst;
         const int32_t ds = k.downsample <= 1 ? 1 : k.downsample;
-        if (k.downsample < 0 || k.downsample > 16 || k.width % ds != 0 || k.height % ds != 0)
-            return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: camera %d downsample %d must be 0..16 and divide %dx%d",
-                        c, k.downsample, k.width, k.height);
-        if (!(k.fx != 0.f) || !(k.fy != 0.f) || !std::isfinite(k.fx) || !std::isfinite(k.fy))
-            return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: camera %d has fx or fy 0", c);
-        if (k.mount_link < 0 || k.mount_link >= v->L)
-            return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: camera %d mount_link %d outside 0..%d", c,
-                        k.mount_link, v->L - 1);
-        if (!(k.d_min <= k.d_max) || !(k.d_max > 0.f) || !std::isfinite(k.d_max))
-            return fail(RPL_ERR_INVALID_ARG, "rpl_cameras_set: camera %d needs 0 < d_max, d_min <= d_max", c);
         v->cam_off[c] = off;
         v->tile_off[c] = toff;
         off += (int64_t)(k.width / ds) * (k.height / ds);
@@ -824,6 +822,9 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
     pp.span = (uint32_t)v->sensor.max_latency + 1u;
     pp.seed0 = v->sensor.seed[0];
     pp.seed1 = v->sensor.seed[1];
+    const bool queued = v->tune.persistent == 2;
+    pp.queues = queued ? v->queues.as<unsigned long long>() : nullptr;
+    pp.n_queues = v->n_queues;
 
     rp = RenderParams{};
     rp.tnodes = s->t_nodes.as<const float4>();
@@ -878,6 +879,8 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
     rp.out = out_dev;
     rp.err = v->err_dev;
     rp.counters = counters_dev;
+    rp.queues = pp.queues;
+    rp.n_queues = pp.n_queues;
     return RPL_OK;
 }
 
@@ -1236,7 +1239,8 @@ static bool tuning_from(const rpl_tuning *t, Tuning *out) {
     if (lg < 0 || t->tile_w * t->tile_h != 32 || (t->min_blocks != 8 && t->min_blocks != 10 && t->min_blocks != 12))
         return false;
     out->tile_w_log2 = lg;
-    out->persistent = t->persistent ? 1 : 0;
+    if (t->persistent < 0 || t->persistent > 2) return false;
+    out->persistent = t->persistent;
     out->terrain_first = t->terrain_first ? 1 : 0;
     out->min_blocks = t->min_blocks;
     return true;
@@ -1254,7 +1258,8 @@ RPL_API rpl_status rpl_view_tuning_set(rpl_view_t v, const rpl_tuning *t) {
     if (!v || !t) return fail(RPL_ERR_INVALID_ARG, "rpl_view_tuning_set: NULL argument");
     Tuning n;
     if (!tuning_from(t, &n))
-        return fail(RPL_ERR_INVALID_ARG, "rpl_view_tuning_set: tile must be 4x8, 8x4 or 16x2 and min_blocks 8, 10 or 12");
+        return fail(RPL_ERR_INVALID_ARG, "rpl_view_tuning_set: tile must be 4x8, 8x4 or 16x2, persistent 0, 1 or 2 "
+                    "and min_blocks 8, 10 or 12");
     v->tune = n;
     return RPL_OK;
 }
@@ -1297,7 +1302,7 @@ RPL_API rpl_status rpl_view_autotune(rpl_view_t v, const float *poses, int64_t s
     float best_v = INFINITY;
     const int tiles[3] = {3, 2, 4};
     for (int ti = 0; ti < 3 && st == RPL_OK; ++ti)
-        for (int pers = 0; pers < 2 && st == RPL_OK; ++pers)
+        for (int pers = 0; pers < 3 && st == RPL_OK; ++pers)
             for (int tf = 0; tf < 2 && st == RPL_OK; ++tf)
                 for (int mb = 8; mb <= 12 && st == RPL_OK; mb += 2) {
                     v->tune = Tuning{tiles[ti], pers, tf, mb};
@@ -1429,6 +1434,29 @@ RPL_API void rpl_view_destroy(rpl_view_t v) {
 
 namespace rpl {
 
+rpl_status check_camera(const rpl_camera &k, int c, int32_t n_links, const char *who) {
+    if (k.width <= 0 || k.height <= 0 || k.width > 16384 || k.height > 16384)
+        return fail(RPL_ERR_INVALID_ARG, "%s: camera %d size %dx%d", who, c, k.width, k.height);
+    const int32_t ds = k.downsample <= 1 ? 1 : k.downsample;
+    if (k.downsample < 0 || k.downsample > 16 || k.width % ds != 0 || k.height % ds != 0)
+        return fail(RPL_ERR_INVALID_ARG, "%s: camera %d downsample %d must be 0..16 and divide %dx%d", who, c,
+                    k.downsample, k.width, k.height);
+    if (!(k.fx != 0.f) || !(k.fy != 0.f) || !std::isfinite(k.fx) || !std::isfinite(k.fy) || !std::isfinite(k.cx) ||
+        !std::isfinite(k.cy))
+        return fail(RPL_ERR_INVALID_ARG, "%s: camera %d needs finite intrinsics with fx, fy != 0", who, c);
+    if (k.mount_link < 0 || k.mount_link >= n_links)
+        return fail(RPL_ERR_INVALID_ARG, "%s: camera %d mount_link %d outside 0..%d", who, c, k.mount_link,
+                    n_links - 1);
+    if (!(k.d_min <= k.d_max) || !(k.d_max > 0.f) || !std::isfinite(k.d_max) || !std::isfinite(k.d_min))
+        return fail(RPL_ERR_INVALID_ARG, "%s: camera %d needs finite 0 < d_max, d_min <= d_max", who, c);
+    double qn = 0.0;
+    for (int a = 0; a < 4; ++a) qn += (double)k.offset_quat_xyzw[a] * k.offset_quat_xyzw[a];
+    if (!std::isfinite(k.offset_pos[0]) || !std::isfinite(k.offset_pos[1]) || !std::isfinite(k.offset_pos[2]) ||
+        !(qn > 0.0) || !std::isfinite(qn))
+        return fail(RPL_ERR_INVALID_ARG, "%s: camera %d needs a finite mount offset and a nonzero quaternion", who, c);
+    return RPL_OK;
+}
+
 bool scene_inputs(const rpl_scene *s, SceneInputs *out) {
     if (!s) return false;
     std::lock_guard<std::mutex> lk(const_cast<rpl_scene *>(s)->mu);
@@ -1463,6 +1491,7 @@ rpl_status view_prepare(rpl_view *v, const float *poses_dev, int64_t step, int64
     PrepParams pp;
     rpl_status s = build_params(v, poses_dev, step, env_offset, out_dev, st, nullptr, nullptr, pp, *rp);
     if (s != RPL_OK) return s;
+    pp.queues = rp->queues = nullptr;   // the fused launch schedules its own tiles
     cudaError_t e = launch_prep(pp, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the prep kernel");
     e = launch_tile_prep(*rp, st);

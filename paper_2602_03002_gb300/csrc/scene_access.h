@@ -23,6 +23,11 @@ bool scene_inputs(const rpl_scene *s, SceneInputs *out);
 // Records the message returned by rpl_last_error() and returns `st`.
 rpl_status set_error(rpl_status st, const char *msg);
 
+// Checks camera c of a camera set for n_links links (size, downsample factor, finite intrinsics with
+// fx, fy != 0, mount link, finite 0 < d_max >= d_min, finite mount offset, nonzero quaternion);
+// on failure records a message naming `who` and returns INVALID_ARG.
+rpl_status check_camera(const rpl_camera &k, int c, int32_t n_links, const char *who);
+
 // Views, for the render server (server.cpp).  view_prepare launches the sensor-state reset (when
 // due) and the prep kernel on `st` and fills the render parameters; warps = tiles of the request.
 rpl_status view_validate(rpl_view *v, const float *poses, int64_t env_offset, void *out);

@@ -89,7 +89,7 @@ EXPORTS = ["rpl_bvh_build_host", "rpl_bvh8_build_host", "rpl_scene_create", "rpl
            "rpl_cameras_set", "rpl_cameras_randomize", "rpl_side_mask_set", "rpl_sensor_set", "rpl_view_state_size",
            "rpl_view_state_get", "rpl_view_state_set", "rpl_view_layout", "rpl_render", "rpl_view_reset", "rpl_sync",
            "rpl_render_counters", "rpl_view_timing", "rpl_view_host_async", "rpl_sensor_apply", "rpl_view_kernel_ms", "rpl_view_destroy", "rpl_last_error",
-           "rpl_version", "rpl_render_static_scratch", "rpl_view_tuning_set", "rpl_view_tuning_get",
+           "rpl_version", "rpl_render_static_scratch", "rpl_static_scratch_status", "rpl_view_tuning_set", "rpl_view_tuning_get",
            "rpl_view_autotune", "rpl_render_graph", "rpl_server_create", "rpl_server_submit", "rpl_server_wait",
            "rpl_server_cancel", "rpl_server_stats_get", "rpl_server_destroy"]
 
@@ -132,6 +132,7 @@ def lib() -> ctypes.CDLL:
         "rpl_last_error": ([], ctypes.c_char_p),
         "rpl_version": ([], I32),
         "rpl_render_static_scratch": ([P, P, I32, I32, I32, P, P, I64, I64, P, P], I32),
+        "rpl_static_scratch_status": ([P, P], I32),
         "rpl_view_tuning_set": ([P, P], I32),
         "rpl_view_tuning_get": ([P, P], I32),
         "rpl_view_autotune": ([P, P, I64, I64, P, P, I32, P, P], I32),
@@ -362,6 +363,12 @@ def rpl_render_static_scratch(scene: int, cams: Sequence, n_envs: int, n_links: 
                                            int(step), int(env_offset), _ptr(out), _stream_handle(stream)))
 
 
+def rpl_static_scratch_status(scene: int, stream=None):
+    """Waits for `stream`, then raises DEVICE_FAULT if a no-allocation render on the scene's device
+    recorded a kernel fault since the last query (the word is cleared by the query)."""
+    _check(lib().rpl_static_scratch_status(scene, _stream_handle(stream)))
+
+
 def rpl_view_tuning_set(view: int, tile_w: int = 8, tile_h: int = 4, persistent: int = 0, terrain_first: int = 0,
                         min_blocks: int = 8):
     t = rpl_tuning(tile_w, tile_h, persistent, terrain_first, min_blocks)
@@ -375,7 +382,7 @@ def rpl_view_tuning_get(view: int) -> dict:
 
 
 def rpl_view_autotune(view: int, poses, step: int, env_offset: int, out, stream=None, reps: int = 3):
-    """Times the 36 launch shapes, keeps the fastest on the view; returns (tuning dict, ms per render)."""
+    """Times the 54 launch shapes, keeps the fastest on the view; returns (tuning dict, ms per render)."""
     t = rpl_tuning()
     ms = ctypes.c_float()
     _check(lib().rpl_view_autotune(view, _ptr(poses), int(step), int(env_offset), _ptr(out), _stream_handle(stream),

@@ -49,7 +49,15 @@ def render_all():
     rpl.View.from_workload(scene, w)
     rpl.rpl_render_static_scratch(scene.h, w.cameras, w.n_envs, w.n_links, poses[0], o)
     torch.cuda.synchronize()
+    rpl.rpl_static_scratch_status(scene.h)   # raises DEVICE_FAULT if the kernels recorded a fault
     out["noalloc"] = o.cpu().numpy()
+    # the per-SM tile-queue launch shape
+    view = rpl.View.from_workload(scene, w)
+    view.set_sensor(sen)
+    rpl.rpl_view_tuning_set(view.h, tile_w=4, tile_h=8, persistent=2, min_blocks=8)
+    for s in range(2):
+        out["queued_step%d" % s] = view.render(poses[s], s).cpu().numpy()
+    view.sync()
     return out
 
 

@@ -1,7 +1,8 @@
 """Batching: uneven cameras in one launch, launch shapes chosen by the autotuner, graph replay.
 
-The launch shape (tile of 32 rays, persistent grid-stride loop, query order, registers per thread)
-must never change the depth: every one of the 36 shapes gives bit-identical frames, also on ragged
+The launch shape (tile of 32 rays, one warp per tile / persistent grid-stride loop / per-SM tile
+queues, query order, registers per thread) must never change the depth: every one of the 54 shapes
+gives bit-identical frames, also on ragged
 cameras where tiles hang over the image edge.  Replaying the captured graph of the whole path must
 continue the sensor history exactly like step-by-step rpl_render calls.
 """
@@ -17,7 +18,7 @@ from paper_2602_03002_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 SHAPES = [dict(tile_w=tw, tile_h=32 // tw, persistent=p, terrain_first=tf, min_blocks=mb)
-          for tw, p, tf, mb in itertools.product((8, 4, 16), (0, 1), (0, 1), (8, 10, 12))]
+          for tw, p, tf, mb in itertools.product((8, 4, 16), (0, 1, 2), (0, 1), (8, 10, 12))]
 
 
 def _ragged(w):
@@ -158,3 +159,28 @@ def test_batching_configuration_at_full_size_in_graph_replay(cuda, rpl_lib):
     got = frames[1][rays[:, 0], o[rays[:, 1]] + rays[:, 3] * cw[rays[:, 1]] + rays[:, 2]]
     compare_depth(got, ref["depth"], ref["flags"], "batching full size")
     assert np.mean(ref["depth"] < 3.0) > 0.3
+
+
+@pytest.mark.parametrize("n_envs,size", [(1, (3, 2)), (2, (13, 7)), (40, (9, 5))])
+def test_per_sm_queues_with_fewer_tiles_than_queues(cuda, rpl_lib, n_envs, size):
+    """Per-SM tile queues when most queues are empty (fewer tiles than SMs) or hold one or two tiles:
+    every tile is still rendered once, giving the frames of the one-warp-per-tile launch."""
+    torch = cuda
+    w = W.config_small(n_steps=2, n_envs=n_envs)
+    torso = w.cameras[0].mount_link
+    w.cameras = [W.pinhole(size[0], size[1], 80.0, 50.0, torso, (0.10, 0.0, 0.30), 0.0, 45.0, 0.1, 3.0)]
+    sen = W.Sensor(sigma_abs=0.01, p_drop=0.05, max_latency=1, seed=(5, 6))
+    scene = rpl_lib.Scene.from_workload(w)
+    view = rpl_lib.View(scene, w.n_envs, w.n_links)
+    view.set_cameras(w.cameras)
+    view.set_sensor(sen)
+    poses = torch.from_numpy(w.poses).cuda()
+    ref = [view.render(poses[s], s).clone() for s in range(2)]
+    for tw in (8, 4, 16):
+        rpl_lib.rpl_view_tuning_set(view.h, tile_w=tw, tile_h=32 // tw, persistent=2)
+        view.reset(None, 0)
+        for s in range(2):
+            out = torch.full_like(ref[s], -1.0)
+            view.render(poses[s], s, 0, out)
+            assert torch.equal(out, ref[s]), (tw, s)
+    view.sync()
