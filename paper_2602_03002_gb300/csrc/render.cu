@@ -418,6 +418,20 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
     if (i < n_link) {
         const int l = (int)(i % p.L);
         const float *q = p.poses + 7 * i;
+        if (l == 0 && p.env_key) {
+            // spatial key of the env: Morton index of link 0's cell on a 64 x 64 grid over the terrain
+            uint32_t cell[2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const float span = p.xy_hi[a] - p.xy_lo[a];
+                const float u = span > 0.f ? (q[a] - p.xy_lo[a]) / span * 64.f : 0.f;
+                cell[a] = u >= 0.f ? (uint32_t)fminf(u, 63.f) : 0u;   // NaN and below the grid -> 0
+            }
+            uint32_t m = 0;
+#pragma unroll
+            for (int b = 0; b < 6; ++b) m |= (((cell[0] >> b) & 1u) << (2 * b)) | (((cell[1] >> b) & 1u) << (2 * b + 1));
+            p.env_key[i / p.L] = m;
+        }
         float R[9];
         quat_rot(q[3], q[4], q[5], q[6], R);
         p.link_xf[3 * i + 0] = make_float4(R[0], R[3], R[6], q[0]);
@@ -529,8 +543,9 @@ struct Ray {
     int kz;               // dominant axis of d
 };
 
+// Correctly rounded reciprocal (the same value as 1.0f / v, with fewer instructions than a division).
 __device__ __forceinline__ float safe_rcp(float v) {
-    return 1.0f / (fabsf(v) > 1e-20f ? v : copysignf(1e-20f, v));
+    return __frcp_rn(fabsf(v) > 1e-20f ? v : copysignf(1e-20f, v));
 }
 
 __device__ __forceinline__ float comp(const float3 &v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
@@ -561,6 +576,37 @@ __device__ __forceinline__ float slab(const Ray &r, float lox, float hix, float 
     const float tin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
     const float tout = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
     return tin <= tout ? tin : CUDART_INF_F;
+}
+
+// Two FP32 fused multiply-adds in one packed instruction (fma.rn.f32x2, sm_100 and later): each lane is
+// an ordinary round-to-nearest fma, so the results equal two fmaf calls.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+// Slab tests of the two child boxes of a binary node (n0: child 0's x and y lo/hi, n1: child 1's, n2:
+// both z lo/hi) against (0, tmax]: the (lo, hi) plane distances of each axis come from one packed fma
+// on the adjacent pair, the same arithmetic as slab().  Returns the entry distances, or +inf for a
+// child the ray misses.
+__device__ __forceinline__ void slab_pair(const float2 &ix, const float2 &iy, const float2 &iz, const float2 &ox,
+                                          const float2 &oy, const float2 &oz, const float4 &n0, const float4 &n1,
+                                          const float4 &n2, float tmax, float &t0, float &t1) {
+    const float2 x0 = fma2(make_float2(n0.x, n0.y), ix, ox), y0 = fma2(make_float2(n0.z, n0.w), iy, oy);
+    const float2 z0 = fma2(make_float2(n2.x, n2.y), iz, oz);
+    const float2 x1 = fma2(make_float2(n1.x, n1.y), ix, ox), y1 = fma2(make_float2(n1.z, n1.w), iy, oy);
+    const float2 z1 = fma2(make_float2(n2.z, n2.w), iz, oz);
+    const float in0 = fmaxf(fmaxf(fminf(x0.x, x0.y), fminf(y0.x, y0.y)), fmaxf(fminf(z0.x, z0.y), 0.0f));
+    const float out0 = fminf(fminf(fmaxf(x0.x, x0.y), fmaxf(y0.x, y0.y)), fminf(fmaxf(z0.x, z0.y), tmax));
+    const float in1 = fmaxf(fmaxf(fminf(x1.x, x1.y), fminf(y1.x, y1.y)), fmaxf(fminf(z1.x, z1.y), 0.0f));
+    const float out1 = fminf(fminf(fmaxf(x1.x, x1.y), fmaxf(y1.x, y1.y)), fminf(fmaxf(z1.x, z1.y), tmax));
+    t0 = in0 <= out0 ? in0 : CUDART_INF_F;
+    t1 = in1 <= out1 ? in1 : CUDART_INF_F;
 }
 
 // Vertex relative to the ray origin, permuted so the dominant axis comes last, then sheared so that
@@ -657,6 +703,11 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
     int cur = root;      // >= 0 inner node, < 0 leaf reference, kDone nothing left
     int pending = 0;     // postponed leaf reference, 0 = none
     auto pop = [&]() -> int { return stack_pop(stack_node, sp); };
+    // the ray's 1/d and -o/d per axis, twice, for the packed slab tests
+    const float2 ix = make_float2(r.invd.x, r.invd.x), iy = make_float2(r.invd.y, r.invd.y),
+                 iz = make_float2(r.invd.z, r.invd.z);
+    const float2 ox = make_float2(-r.oinv.x, -r.oinv.x), oy = make_float2(-r.oinv.y, -r.oinv.y),
+                 oz = make_float2(-r.oinv.z, -r.oinv.z);
 #pragma unroll 1
     for (;;) {
 #pragma unroll 1
@@ -666,8 +717,8 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
             const float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2);
             const int4 n3 = __ldg(reinterpret_cast<const int4 *>(n + 3));
             if (kCount) ++cnt.nodes;
-            float t0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tmax);
-            float t1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tmax);
+            float t0, t1;
+            slab_pair(ix, iy, iz, ox, oy, oz, n0, n1, n2, tmax, t0, t1);
             // leaf children arrive encoded and empty ones never hit (device layout, see rpl_api.cpp)
             const int e0 = n3.x, e1 = n3.y;
             const bool h0 = t0 != CUDART_INF_F, h1 = t1 != CUDART_INF_F;
@@ -1006,7 +1057,11 @@ __device__ __forceinline__ void finish_pixel(const RenderParams &p, int e, int c
         if (z < cam.d_max) {
             const float u1 = ((float)w.y + 1.0f) * 0x1p-32f;
             const float u2 = (float)w.z * 0x1p-32f;
-            const float n = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+            // cos(2 pi u2) by the hardware cosine on [-pi, pi) (absolute error below 5e-7, i.e. below
+            // 1e-6 m of depth for noise scales up to 1 m); the logarithm stays exact to an ulp, since
+            // near u1 = 1 an absolute error of the fast one would reach the depth tolerance
+            const float a = 6.2831853071795864f * (u2 >= 0.5f ? u2 - 1.0f : u2);
+            const float n = sqrtf(-2.0f * logf(u1)) * __cosf(a);
             z = z + (p.sigma_abs + p.sigma_rel * z) * n;
         }
         z = fminf(fmaxf(z, cam.d_min), cam.d_max);
@@ -1081,6 +1136,15 @@ __device__ __forceinline__ void tile_reach_in_warp(const RenderParams &p, int e,
         link_mask |= (uint64_t)__ballot_sync(0xffffffffu, keep) << (32 * half);
         if ((cam_mask >> 32) == 0) break;
     }
+}
+
+// Tile index (env * tiles_per_env + tile within the env) of the t-th tile in processing order: the
+// envs in p.env_order's order when it is set, else in index order.
+__device__ __forceinline__ int64_t tile_of(const RenderParams &p, int64_t t) {
+    if (!p.env_order) return t;
+    int e, r;
+    split_tile(t, p.tiles_per_env, e, r);
+    return (int64_t)__ldg(p.env_order + e) * p.tiles_per_env + r;
 }
 
 // One warp renders one tile of 32 pixel rays (tile_w x tile_h, tile_w = 2^tile_w_log2) of one
@@ -1230,6 +1294,29 @@ __device__ __forceinline__ int64_t queue_begin(int64_t total, int q, int nq) {
     return base * q + min((int64_t)q, rem);
 }
 
+// Tiles of queue q: a contiguous range (chunk == 0), or chunks q, q + nq, q + 2 nq, ... of `chunk`
+// tiles each (the last chunk of all may be short).
+__device__ __forceinline__ int64_t queue_size(int64_t total, int q, int nq, int64_t chunk) {
+    if (chunk <= 0) return queue_begin(total, q + 1, nq) - queue_begin(total, q, nq);
+    const int64_t nc = (total + chunk - 1) / chunk;
+    if (q >= nc) return 0;
+    const int64_t mine = (nc - 1 - q) / nq + 1;           // chunks of queue q
+    const int64_t last = q + (mine - 1) * nq;
+    return mine * chunk - (last == nc - 1 ? nc * chunk - total : 0);
+}
+
+// Processing-order position of the k-th tile of queue q (k < queue_size); b = queue_begin(total, q,
+// nq) when chunk == 0.  32-bit division whenever the operands fit.
+__device__ __forceinline__ int64_t queue_tile(int q, int nq, int64_t chunk, int64_t b, int64_t k) {
+    if (chunk <= 0) return b + k;
+    int64_t j;
+    if ((uint64_t)k < 0x100000000ull && (uint64_t)chunk < 0x100000000ull)
+        j = (int64_t)((uint32_t)k / (uint32_t)chunk);
+    else
+        j = k / chunk;
+    return (q + j * nq) * chunk + (k - j * chunk);
+}
+
 // Per-SM scheduling (p.queues set): the tiles are split into p.n_queues contiguous queues, one per
 // SM.  A warp takes the next tile of its SM's queue (one atomic per tile), so the SM's warps work on
 // neighbouring tiles of the same images, whose terrain nodes they share in L1; a warp whose block
@@ -1240,24 +1327,26 @@ __device__ __forceinline__ int64_t queue_begin(int64_t total, int q, int nq) {
 template <bool kCount, int kKind, bool kTileInfo>
 __device__ __forceinline__ void render_queued(const RenderParams &p, int lane, int64_t total, int64_t step) {
     const int nq = p.n_queues;
+    const int64_t chunk = (int64_t)p.chunk_envs * p.tiles_per_env;
     uint32_t smid;
     asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
     int q = (int)(smid % (uint32_t)nq);
+    int64_t qsize = queue_size(total, q, nq, chunk), qbegin = queue_begin(total, q, nq);
 #pragma unroll 1
     for (;;) {
         unsigned long long k = 0ull;
         if (lane == 0) k = atomicAdd(p.queues + q, 1ull);
         k = __shfl_sync(0xffffffffu, k, 0);
-        const int64_t b = queue_begin(total, q, nq), size = queue_begin(total, q + 1, nq) - b;
-        if (k < (unsigned long long)size) {
-            render_tile<kCount, kKind, kTileInfo>(p, b + (int64_t)k, lane, step);
+        if (k < (unsigned long long)qsize) {
+            render_tile<kCount, kKind, kTileInfo>(p, tile_of(p, queue_tile(q, nq, chunk, qbegin, (int64_t)k)), lane,
+                                                  step);
             continue;
         }
         // this queue is empty: the queue with the most tiles left (warp-wide argmax)
         int64_t best = 0;
         int best_q = -1;
         for (int j = lane; j < nq; j += 32) {
-            const int64_t sz = queue_begin(total, j + 1, nq) - queue_begin(total, j, nq);
+            const int64_t sz = queue_size(total, j, nq, chunk);
             const unsigned long long taken = __ldcg(p.queues + j);
             const int64_t left = taken < (unsigned long long)sz ? sz - (int64_t)taken : 0;
             if (left > best) {
@@ -1276,6 +1365,8 @@ __device__ __forceinline__ void render_queued(const RenderParams &p, int lane, i
         }
         if (best <= 0) return;
         q = best_q;
+        qsize = queue_size(total, q, nq, chunk);
+        qbegin = queue_begin(total, q, nq);
     }
 }
 
@@ -1291,7 +1382,7 @@ __global__ void __launch_bounds__(128, kMinBlocks) render_kernel(const __grid_co
     const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 5);
 #pragma unroll 1
     for (int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); warp < total; warp += stride)
-        render_tile<kCount, kKind, kTileInfo>(p, warp, lane, step);
+        render_tile<kCount, kKind, kTileInfo>(p, tile_of(p, warp), lane, step);
 }
 
 // Terrain entry node and link mask of every tile, one thread per tile of 32 rays (the same work done
@@ -1468,6 +1559,54 @@ __global__ void set_first_kernel(int64_t *s_first, int32_t E, int64_t step, cons
     if (i < E && (mask == nullptr || mask[i] != 0)) s_first[i] = step;
 }
 
+// Counting sort of the envs by their spatial key in one block: histogram of the kOrderBuckets keys in
+// shared memory, exclusive prefix sum, then each env's slot by an atomic increment of its bucket's
+// offset (so the order inside a bucket is arbitrary).
+__global__ void __launch_bounds__(1024) env_order_kernel(const uint32_t *__restrict__ key, int32_t *__restrict__ order,
+                                                         int32_t E) {
+    constexpr int kPer = kOrderBuckets / 1024;
+    __shared__ uint32_t h[kOrderBuckets];
+    __shared__ uint32_t warp_sum[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    for (int i = t; i < kOrderBuckets; i += 1024) h[i] = 0u;
+    __syncthreads();
+    for (int e = t; e < E; e += 1024) atomicAdd(&h[__ldg(key + e) & (kOrderBuckets - 1)], 1u);
+    __syncthreads();
+    // exclusive scan: each thread owns kPer consecutive buckets
+    uint32_t v[kPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        v[k] = h[t * kPer + k];
+        sum += v[k];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, inc, s);
+        if (lane >= s) inc += o;
+    }
+    if (lane == 31) warp_sum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = warp_sum[lane], wi = w;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, wi, s);
+            if (lane >= s) wi += o;
+        }
+        warp_sum[lane] = wi - w;   // exclusive prefix of the warps
+    }
+    __syncthreads();
+    uint32_t run = warp_sum[wid] + inc - sum;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        h[t * kPer + k] = run;
+        run += v[k];
+    }
+    __syncthreads();
+    for (int e = t; e < E; e += 1024) order[atomicAdd(&h[__ldg(key + e) & (kOrderBuckets - 1)], 1u)] = e;
+}
+
 }  // namespace
 
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s) {
@@ -1589,6 +1728,13 @@ cudaError_t launch_render_multi(const RenderParams *reqs_dev, const int64_t *pre
         launch_multi_kind<RPL_BVH4>(reqs_dev, prefix_dev, n_req, mb, g, s);
     else
         launch_multi_kind<RPL_BVH2>(reqs_dev, prefix_dev, n_req, mb, g, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_env_order(const uint32_t *key, int32_t *order, int32_t E, cudaStream_t s) {
+    if (E <= 0) return cudaSuccess;
+    (void)cudaGetLastError();
+    env_order_kernel<<<1, 1024, 0, s>>>(key, order, E);
     return cudaGetLastError();
 }
 

@@ -53,7 +53,14 @@ struct PrepParams {
     // null otherwise
     unsigned long long *queues;
     int32_t n_queues;
+    // spatial key of each env for the processing order (Tuning::env_order), or null: the Morton index
+    // of link 0's position on a 64 x 64 grid over the terrain's xy extent [xy_lo, xy_hi]
+    uint32_t *env_key;
+    float xy_lo[2], xy_hi[2];
 };
+
+// Number of spatial buckets of the env processing order (64 x 64 cells in Morton order).
+constexpr int kOrderBuckets = 4096;
 
 // Launch shape of the render kernel (chosen by the autotuner or set by the caller).
 struct Tuning {
@@ -64,6 +71,10 @@ struct Tuning {
                              // then from the fullest other queue
     int32_t terrain_first;   // query the terrain before the links
     int32_t min_blocks;      // 8 (64 registers) or 12 (40 registers) blocks of 128 per SM
+    int32_t env_order;       // 1: tiles are processed env by env in the spatial order of the envs
+                             // (sorted by position each render), 0: in env index order
+    int32_t chunk_envs;      // persistent == 2 only: 0 = one contiguous range of tiles per queue; > 0 =
+                             // chunks of the tiles of this many envs dealt to the queues in turn
 };
 
 struct RenderParams {
@@ -109,9 +120,12 @@ struct RenderParams {
     int32_t *err;                   // error word (1: traversal stack overflow, 4: index out of range)
     unsigned long long *counters;   // rpl_counters fields, or null
     // per-SM tile queues (persistent == 2): n_queues counters of tiles taken, zeroed by the prep
-    // kernel; the tiles are split into n_queues contiguous queues of near-equal size; null otherwise
+    // kernel; the tiles are split into n_queues contiguous queues of near-equal size (chunk_envs 0)
+    // or dealt to them in chunks of the tiles of chunk_envs envs; null otherwise
     unsigned long long *queues;
-    int32_t n_queues;
+    int32_t n_queues, chunk_envs;
+    // processing order of the envs ([E] env indices, sorted by position), or null for index order
+    const int32_t *env_order;
     // fused launches only (render_multi_kernel): tiles of this request still running, and a word in
     // host-mapped memory set to 1 when the last of them has stored its pixels; null when unused
     int32_t *done_counter;
@@ -119,6 +133,9 @@ struct RenderParams {
 };
 
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s);
+// Env processing order: order[0..E) = the envs sorted by key[e] (kOrderBuckets buckets; the order
+// inside a bucket is arbitrary and does not affect any result).  Runs after launch_prep.
+cudaError_t launch_env_order(const uint32_t *key, int32_t *order, int32_t E, cudaStream_t s);
 // Per-tile terrain entry nodes and link masks into p.tile_info (no-op when it is null).  Runs after
 // launch_prep and before launch_render of the same parameters.
 cudaError_t launch_tile_prep(const RenderParams &p, cudaStream_t s);

@@ -161,6 +161,7 @@ struct rpl_scene {
     std::vector<HostBvh> links;      // indexed by link id
     std::vector<bool> has_link;
     DevBuf l_nodes, l_tris, l_roots;
+    float xy_lo[2] = {0.f, 0.f}, xy_hi[2] = {1.f, 1.f};   // xy extent of the terrain's vertices
     int32_t l_root[RPL_MAX_LINKS];
     int64_t l_n_nodes = 0, l_n_tris = 0;
     int32_t l_depth = 0;
@@ -197,6 +198,8 @@ struct rpl_view {
     // per-SM tile queues of the render kernel (launch shape persistent == 2): one counter per SM
     DevBuf queues;
     int32_t n_queues = 0;
+    // spatial processing order of the envs (launch shape env_order == 1): key and order [E]
+    DevBuf env_key, env_order;
     int64_t raw_off[RPL_MAX_CAMERAS] = {};
     DevBuf mount_dr;                 // [E, C, 7] per-env mount perturbation (rpl_cameras_randomize)
     DevBuf rsm_mode;                 // [E] side-mask modes (rpl_side_mask_set)
@@ -216,8 +219,10 @@ struct rpl_view {
     bool timing = false;
     cudaEvent_t ev[2 * kTimingSlots] = {};
     int64_t n_timed = 0;
-    // launch shape of the render kernel
-    Tuning tune{3, 0, 0, 8};
+    // launch shape of the render kernel: 4x8 tiles, per-SM tile queues dealt one env at a time in the
+    // spatial order of the envs, links first, 8 blocks per SM (the fastest shape of the autotuner's
+    // sweep on the 4096-env scale workload)
+    Tuning tune{2, 2, 0, 8, 1, 1};
     // graph replay (rpl_render_graph): device step counter, captured graph and what it was captured for
     DevBuf d_step;
     int64_t dev_step_next = INT64_MIN; // value the device counter holds before the next replay
@@ -270,6 +275,19 @@ RPL_API rpl_status rpl_scene_create(const float *verts, int64_t n_verts, const i
     if (!s) return fail(RPL_ERR_OUT_OF_MEMORY, "rpl_scene_create: host allocation");
     s->device = o.device;
     s->opts = o;
+    {
+        // xy extent of the terrain (for the spatial order of the envs)
+        const float *vp = reinterpret_cast<const float *>(hv.data());
+        bool any = false;
+        for (int64_t i = 0; i < n_verts; ++i)
+            for (int a = 0; a < 2; ++a) {
+                const float x = vp[3 * i + a];
+                if (!std::isfinite(x)) continue;
+                if (!any || x < s->xy_lo[a]) s->xy_lo[a] = x;
+                if (!any || x > s->xy_hi[a]) s->xy_hi[a] = x;
+                if (a == 1) any = true;
+            }
+    }
     s->links.resize(RPL_MAX_LINKS);
     s->has_link.assign(RPL_MAX_LINKS, false);
     for (int l = 0; l < RPL_MAX_LINKS; ++l) s->l_root[l] = -1;
@@ -563,6 +581,8 @@ RPL_API rpl_status rpl_view_create(rpl_scene_t s, int32_t n_envs, int32_t n_link
         v->n_queues = std::max(1, v->n_queues);
         e = v->queues.alloc((size_t)v->n_queues * sizeof(unsigned long long));
     }
+    if (e == cudaSuccess) e = v->env_key.alloc(std::max<size_t>((size_t)n_envs, 1) * sizeof(uint32_t));
+    if (e == cudaSuccess) e = v->env_order.alloc(std::max<size_t>((size_t)n_envs, 1) * sizeof(int32_t));
     if (e != cudaSuccess) {
         if (v->err_host) cudaFreeHost(v->err_host);
         if (v->done) cudaEventDestroy(v->done);
@@ -825,6 +845,11 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
     const bool queued = v->tune.persistent == 2;
     pp.queues = queued ? v->queues.as<unsigned long long>() : nullptr;
     pp.n_queues = v->n_queues;
+    pp.env_key = v->tune.env_order ? v->env_key.as<uint32_t>() : nullptr;
+    for (int a = 0; a < 2; ++a) {
+        pp.xy_lo[a] = s->xy_lo[a];
+        pp.xy_hi[a] = s->xy_hi[a];
+    }
 
     rp = RenderParams{};
     rp.tnodes = s->t_nodes.as<const float4>();
@@ -881,6 +906,8 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
     rp.counters = counters_dev;
     rp.queues = pp.queues;
     rp.n_queues = pp.n_queues;
+    rp.chunk_envs = v->tune.chunk_envs;
+    rp.env_order = v->tune.env_order ? v->env_order.as<const int32_t>() : nullptr;
     return RPL_OK;
 }
 
@@ -894,6 +921,10 @@ static rpl_status enqueue(rpl_view *v, const float *poses_dev, int64_t step, int
     if (stt != RPL_OK) return stt;
     cudaError_t e = launch_prep(pp, st);
     if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the prep kernel");
+    if (pp.env_key) {
+        e = launch_env_order(pp.env_key, v->env_order.as<int32_t>(), v->E, st);
+        if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the env-order kernel");
+    }
     e = launch_tile_prep(rp, st);
     if (e != cudaSuccess) return cuda_fail(e, "rpl_render: launching the tile-prep kernel");
     const int slot = (int)(v->n_timed % rpl_view::kTimingSlots);
@@ -1239,8 +1270,12 @@ static bool tuning_from(const rpl_tuning *t, Tuning *out) {
     if (lg < 0 || t->tile_w * t->tile_h != 32 || (t->min_blocks != 8 && t->min_blocks != 10 && t->min_blocks != 12))
         return false;
     out->tile_w_log2 = lg;
-    if (t->persistent < 0 || t->persistent > 2) return false;
+    if (t->persistent < 0 || t->persistent > 2 || t->env_order < 0 || t->env_order > 1 || t->chunk_envs < 0 ||
+        t->chunk_envs > (1 << 20))
+        return false;
     out->persistent = t->persistent;
+    out->env_order = t->env_order;
+    out->chunk_envs = t->chunk_envs;
     out->terrain_first = t->terrain_first ? 1 : 0;
     out->min_blocks = t->min_blocks;
     return true;
@@ -1252,14 +1287,16 @@ static void tuning_to(const Tuning &t, rpl_tuning *out) {
     out->persistent = t.persistent;
     out->terrain_first = t.terrain_first;
     out->min_blocks = t.min_blocks;
+    out->env_order = t.env_order;
+    out->chunk_envs = t.chunk_envs;
 }
 
 RPL_API rpl_status rpl_view_tuning_set(rpl_view_t v, const rpl_tuning *t) {
     if (!v || !t) return fail(RPL_ERR_INVALID_ARG, "rpl_view_tuning_set: NULL argument");
     Tuning n;
     if (!tuning_from(t, &n))
-        return fail(RPL_ERR_INVALID_ARG, "rpl_view_tuning_set: tile must be 4x8, 8x4 or 16x2, persistent 0, 1 or 2 "
-                    "and min_blocks 8, 10 or 12");
+        return fail(RPL_ERR_INVALID_ARG, "rpl_view_tuning_set: tile must be 4x8, 8x4 or 16x2, persistent 0, 1 or 2, "
+                    "min_blocks 8, 10 or 12, env_order 0 or 1 and chunk_envs 0..2^20");
     v->tune = n;
     return RPL_OK;
 }
@@ -1301,11 +1338,14 @@ RPL_API rpl_status rpl_view_autotune(rpl_view_t v, const float *poses, int64_t s
     Tuning best_t = saved;
     float best_v = INFINITY;
     const int tiles[3] = {3, 2, 4};
+    // (persistent, env_order, chunk_envs): index order or spatial order for each scheduling, and the
+    // per-SM queues as contiguous ranges or dealt one env at a time
+    const int sched[8][3] = {{0, 0, 0}, {0, 1, 0}, {1, 0, 0}, {1, 1, 0}, {2, 0, 0}, {2, 1, 0}, {2, 0, 1}, {2, 1, 1}};
     for (int ti = 0; ti < 3 && st == RPL_OK; ++ti)
-        for (int pers = 0; pers < 3 && st == RPL_OK; ++pers)
+        for (int sc = 0; sc < 8 && st == RPL_OK; ++sc)
             for (int tf = 0; tf < 2 && st == RPL_OK; ++tf)
                 for (int mb = 8; mb <= 12 && st == RPL_OK; mb += 2) {
-                    v->tune = Tuning{tiles[ti], pers, tf, mb};
+                    v->tune = Tuning{tiles[ti], sched[sc][0], tf, mb, sched[sc][1], sched[sc][2]};
                     st = enqueue(v, poses, step, env_offset, out, cs, false, nullptr);   // warm-up
                     if (st != RPL_OK) break;
                     cudaEventRecord(a, cs);
@@ -1492,6 +1532,8 @@ rpl_status view_prepare(rpl_view *v, const float *poses_dev, int64_t step, int64
     rpl_status s = build_params(v, poses_dev, step, env_offset, out_dev, st, nullptr, nullptr, pp, *rp);
     if (s != RPL_OK) return s;
     pp.queues = rp->queues = nullptr;   // the fused launch schedules its own tiles
+    pp.env_key = nullptr;
+    rp->env_order = nullptr;
     cudaError_t e = launch_prep(pp, st);
     if (e != cudaSuccess) return cuda_fail(e, "launching the prep kernel");
     e = launch_tile_prep(*rp, st);

@@ -62,7 +62,8 @@ class rpl_scene_info(ctypes.Structure):
 
 class rpl_tuning(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("persistent", ctypes.c_int32),
-                ("terrain_first", ctypes.c_int32), ("min_blocks", ctypes.c_int32)]
+                ("terrain_first", ctypes.c_int32), ("min_blocks", ctypes.c_int32), ("env_order", ctypes.c_int32),
+                ("chunk_envs", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -369,9 +370,9 @@ def rpl_static_scratch_status(scene: int, stream=None):
     _check(lib().rpl_static_scratch_status(scene, _stream_handle(stream)))
 
 
-def rpl_view_tuning_set(view: int, tile_w: int = 8, tile_h: int = 4, persistent: int = 0, terrain_first: int = 0,
-                        min_blocks: int = 8):
-    t = rpl_tuning(tile_w, tile_h, persistent, terrain_first, min_blocks)
+def rpl_view_tuning_set(view: int, tile_w: int = 4, tile_h: int = 8, persistent: int = 2, terrain_first: int = 0,
+                        min_blocks: int = 8, env_order: int = 1, chunk_envs: int = 1):
+    t = rpl_tuning(tile_w, tile_h, persistent, terrain_first, min_blocks, env_order, chunk_envs)
     _check(lib().rpl_view_tuning_set(view, ctypes.byref(t)))
 
 
@@ -382,7 +383,7 @@ def rpl_view_tuning_get(view: int) -> dict:
 
 
 def rpl_view_autotune(view: int, poses, step: int, env_offset: int, out, stream=None, reps: int = 3):
-    """Times the 54 launch shapes, keeps the fastest on the view; returns (tuning dict, ms per render)."""
+    """Times the 144 launch shapes, keeps the fastest on the view; returns (tuning dict, ms per render)."""
     t = rpl_tuning()
     ms = ctypes.c_float()
     _check(lib().rpl_view_autotune(view, _ptr(poses), int(step), int(env_offset), _ptr(out), _stream_handle(stream),
