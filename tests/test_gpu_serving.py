@@ -262,3 +262,61 @@ def test_cancel_while_another_thread_waits(cuda, rpl_lib):
     st = server.stats()
     server.close()
     assert st["submitted"] == 3 and st["failed"] == 0
+
+
+def test_served_results_match_the_oracle(cuda, rpl_lib):
+    """Requests of different env counts and camera sets, with device and pinned host buffers, fused by
+    the server into shared launches, compared with the FP64 oracle over three steps with latency,
+    noise and dropout: every served frame within the tolerance, dropout decisions bit-exact.  A large
+    request occupies the only stream slot while the others are submitted, so they queue and go out
+    fused; the server's statistics confirm it."""
+    import oracle
+    from conftest import compare_depth
+    torch = cuda
+    w = _workload()
+    scene = rpl_lib.Scene.from_workload(w)
+    shapes = [(5, 1), (9, 2), (16, 4), (3, 3), (7, 2), (12, 1)]
+    views = _views(rpl_lib, torch, w, scene, shapes)
+    big_w = W.config_small(n_steps=1, n_envs=16384)
+    blocker = rpl_lib.View(scene, 16384, w.n_links)
+    blocker.set_cameras(w.cameras)
+    pb = torch.from_numpy(np.ascontiguousarray(big_w.poses[0])).cuda()
+    ob = blocker.out_tensor()
+    server = rpl_lib.Server(scene, max_batch=8, n_streams=1)
+    served = {}
+    fused = []
+    import time
+    for s in range(3):
+        before = server.stats()["batches"]
+        t0 = server.submit(blocker, pb, s, ob)
+        deadline = time.time() + 5.0
+        while server.stats()["batches"] == before and time.time() < deadline:   # the blocker is on the GPU
+            time.sleep(0.0001)
+        tickets = []
+        for k, (v, poses, E, C) in enumerate(views):
+            if (s + k) % 2:
+                out, src = v.out_tensor(), poses[s]
+            else:
+                out = torch.empty((E, v.layout()[1]), dtype=torch.float32).pin_memory()
+                src = poses[s].cpu().pin_memory()
+            tickets.append((k, server.submit(v, src, s, out, 100 * k), out, src))
+        server.wait(t0)
+        for k, tk, out, src in tickets:
+            server.wait(tk)
+            served[(k, s)] = out.cpu().numpy().reshape(-1).copy()
+        fused.append(server.stats()["max_batch_seen"])
+    st = server.stats()
+    server.close()
+    assert st["failed"] == 0 and st["max_batch_seen"] >= 2, st
+    for k, (v, poses, E, C) in enumerate(views):
+        envs = (np.arange(E) * 3 + k) % w.n_envs
+        osc = oracle.OracleScene.from_workload(w)
+        rays = oracle.all_rays(w.cameras[:C], E)
+        for s in range(3):
+            ref = osc.render(w.cameras[:C], np.ascontiguousarray(w.poses[:, envs]), s, rays, SENSOR,
+                             s_first=np.zeros(E, np.int64), env_offset=100 * k)
+            got = served[(k, s)]
+            dropped = (ref["flags"] & oracle.FLAG_DROPPED) != 0
+            assert np.array_equal(got == np.float32(SENSOR.fill), dropped), (k, s)
+            compare_depth(got, ref["depth"], ref["flags"], "served request %d (%d envs x %d cams) step %d" % (k, E, C, s))
+        osc.close()

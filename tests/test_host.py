@@ -279,3 +279,36 @@ def test_perception_generators():
     for sel, probs in ((~stones, W.RSM_PROBS["continuous"]), (stones, W.RSM_PROBS["stones"])):
         freq = np.bincount(modes[sel], minlength=3) / sel.sum()
         assert np.all(np.abs(freq - np.asarray(probs)) < 5 * np.sqrt(0.25 / sel.sum()))
+
+
+def test_camera_randomization_conversions_by_an_independent_route():
+    """The perception draws (Appendix A.2) are converted to a mount quaternion and per-env intrinsics in
+    the shared input generator.  Checked here by other routes: the quaternion against scipy's intrinsic
+    z-x-y Euler composition of the same draws (roll about the optical axis, pitch about the right axis,
+    yaw about the down axis), its angles recovered by scipy within the stated ranges and spread over
+    them; and the focal lengths through the field of view they span, (W / 2) / tan(hfov' / 2), which
+    must be the camera's horizontal FOV plus the drawn change, with square pixels and the principal
+    point unchanged."""
+    from scipy import stats
+    cams = W.perception_cameras(0, 2, raw=(240, 135), downsample=5)
+    E, seed = 4096, 11
+    mount, intr = W.camera_randomization(E, cams, seed=seed)
+    # the draws, in the generator's order (its seeded stream: translation, three angles, FOV change)
+    rng = np.random.default_rng(seed + 17)
+    dp = rng.uniform(-0.025, 0.025, size=(E, 2, 3))
+    ang = np.stack([rng.uniform(-a, a, size=(E, 2)) for a in (2.5, 3.0, 2.5)], axis=-1)
+    dfov = rng.uniform(-2.0, 2.0, size=(E, 2))
+    np.testing.assert_allclose(mount[..., :3], dp, rtol=0, atol=1e-7)
+    q = Rotation.from_euler("ZXY", ang.reshape(-1, 3), degrees=True).as_quat().reshape(E, 2, 4)
+    sign = np.sign(np.sum(q * mount[..., 3:], axis=-1, keepdims=True))
+    np.testing.assert_allclose(mount[..., 3:], sign * q, rtol=0, atol=2e-7)
+    back = Rotation.from_quat(mount[..., 3:].reshape(-1, 4)).as_euler("ZXY", degrees=True)
+    for k, bound in enumerate((2.5, 3.0, 2.5)):
+        assert np.abs(back[:, k]).max() <= bound + 1e-4 and np.abs(back[:, k]).max() > 0.99 * bound
+        assert stats.kstest(back[:, k], stats.uniform(-bound, 2 * bound).cdf).pvalue > 1e-3
+    for c, cam in enumerate(cams):
+        hfov = 2.0 * np.degrees(np.arctan(cam.width / (2.0 * cam.fx)))
+        spanned = 2.0 * np.degrees(np.arctan(cam.width / (2.0 * intr[:, c, 0].astype(np.float64))))
+        np.testing.assert_allclose(spanned - hfov, dfov[:, c], rtol=0, atol=2e-4)
+        np.testing.assert_allclose(intr[:, c, 1] / cam.fy, intr[:, c, 0] / cam.fx, rtol=2e-7)
+        assert np.all(intr[:, c, 2] == np.float32(cam.cx)) and np.all(intr[:, c, 3] == np.float32(cam.cy))

@@ -1,9 +1,10 @@
-"""Env sharding across ranks (CPU, gloo, world size 2).
+"""The env-sharding convention across ranks, on CPU (gloo, world size 2), with the oracle.
 
 Each rank renders its own range of envs with env_offset = its first global env id, so the random
 streams (keyed by global env id) and hence the outputs do not depend on how envs are spread over
 processes.  The gather below only checks the result; the render path itself has no collective.
-The renderer here is the oracle (the CPU stand-in for a rank's GPU).
+This test checks the keying convention with the FP64 oracle as each rank's renderer; the library
+itself is run the same way, two processes on one GPU, in test_gpu_multiprocess.py.
 """
 import os
 import socket
