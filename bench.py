@@ -40,7 +40,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Grays/s and depth frames/s at 4096 envs; serve p50/p99 latency vs plain FP32"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC = os.path.join(ROOT, "profiles", "render_kernel_traffic.json")
+# ncu counters of single render_kernel launches of the bench's own workloads (full size, no scaling)
+COUNTERS = os.path.join(ROOT, "profiles", "render_kernel_counters.json")
+SMSP_PER_SM = 4   # warp schedulers per SM, each issuing at most one warp instruction per cycle
 TRI_BYTES, BOX_BYTES = 48, 32
 
 
@@ -55,9 +57,14 @@ def parse():
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--tiles", type=int, default=20)
     ap.add_argument("--pose-sets", type=int, default=8)
-    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
+    ap.add_argument("--autotune", action="store_true",
+                    help="plain variant: run the library's autotuner instead of its default launch shape")
+    ap.add_argument("--no-serve", action="store_true", help="leave out the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=400, help="requests per form in the serve object")
     ap.add_argument("--tuning", default=None,
-                    help="fixed launch shape tile_w,tile_h,persistent,terrain_first,min_blocks (skips the autotuner)")
+                    help="fixed launch shape tile_w,tile_h,persistent,terrain_first,min_blocks[,env_order,chunk_tiles] "
+                         "(skips the autotuner)")
     ap.add_argument("--bvh", type=int, default=None, choices=[2, 4, 8],
                     help="terrain BVH layout: 2 binary, 4 four-wide FP32, 8 eight-wide quantised "
                          "(default: 8 for precision, else 2)")
@@ -138,20 +145,87 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(rays, variant, tuning, bvh):
-    """DRAM bytes per launch from the committed ncu capture, scaled by rays; None if the kernel, the
-    variant or the launch shape differ from what was captured."""
+def counters_for_launch(rays, variant, tuning, bvh):
+    """The committed ncu counters of one render_kernel launch of exactly this workload: same kernel
+    source hash, variant, terrain BVH layout, launch shape and rays per launch (no scaling).  None
+    when no capture matches (the kernel or the workload changed since the counters were taken)."""
     try:
-        with open(TRAFFIC) as f:
+        with open(COUNTERS) as f:
             entries = json.load(f)["captures"]
     except Exception:
         return None
     sha = kernel_hash()
     for t in entries:
         if (t.get("kernel_sha") == sha and t.get("variant") == variant and t.get("tuning") == tuning
-                and t.get("bvh", 2) == bvh):
-            return float(t["dram_bytes"]) * rays / float(t["rays"])
+                and t.get("bvh", 2) == bvh and int(t.get("rays", -1)) == int(rays)):
+            return t
     return None
+
+
+def l2_copy_gbs(dev):
+    """Copy bandwidth of a 2 x 24 MiB buffer pair, which stays in the 129 MB L2: read + write bytes over
+    the best of 30 copies (torch's copy kernel, CUDA events).  The L2 counterpart of the HBM copy peak."""
+    import torch
+    n = 24 << 18                                   # float32 elements in 24 MiB
+    a = torch.ones(n, device=f"cuda:{dev}")
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    best = float("inf")
+    for _ in range(30):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return 2 * 4 * n / best / 1e9
+
+
+def roofline(ctr, k_s, alg_bytes, rays, sms, clock_mhz, l2_peak, cnt):
+    """Roofline of the render kernel against the resource that binds.  From the committed counters of
+    this launch: DRAM bytes against the measured HBM copy peak, L2 bytes against the L2 copy peak
+    measured in this run, and warp instructions against the issue capacity (SMs x 4 schedulers x the
+    SM clock sampled during the timed region), each divided by the launch's CUDA-event time.  `bound`
+    names the highest of the three fractions and the top-level figures are that resource's.  The
+    traversal's fetch bytes per ray (nodes, triangles, link boxes; counting kernel) are kept as
+    fetch_bytes_per_ray: most of them are served by L1/L2, so they are not an HBM figure."""
+    hbm_peak, hbm_src = peaks()
+    out = {"kernel": "render_kernel", "kernel_ms": 1e3 * k_s,
+           "fetch_bytes_per_ray": alg_bytes / rays,
+           "fetch_note": "node (64 B), triangle (48 B) and link-box (32 B) fetches of the traversal per ray plus "
+                         "its output and ring bytes, from the counting kernel; most are L1/L2 hits",
+           "per_ray": {k: cnt[k] / rays for k in ("terrain_nodes", "terrain_tris", "link_boxes",
+                                                  "link_nodes", "link_tris")}}
+    if ctr is None:
+        out.update({"bound": None, "achieved": None, "peak": hbm_peak, "unit": "GB/s", "frac": None,
+                    "traffic": None, "counters": "no committed ncu capture of this kernel source, workload and "
+                                                 "launch shape"})
+        return out
+    issue_peak = sms * SMSP_PER_SM * clock_mhz * 1e6
+    res = {
+        "hbm": {"achieved": ctr["dram_bytes"] / k_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "peak_source": hbm_src + " hbm_gbs (copy)"},
+        "l2": {"achieved": ctr["lts_bytes"] / k_s / 1e9, "peak": l2_peak, "unit": "GB/s",
+               "peak_source": "measured in this run: copy of a 2 x 24 MiB buffer pair resident in L2"},
+        "issue": {"achieved": ctr["inst_executed"] / k_s / 1e9, "peak": issue_peak / 1e9,
+                  "unit": "G warp-instructions/s",
+                  "peak_source": "%d SMs x %d schedulers x %.0f MHz (SM clock sampled during the timed region)"
+                                 % (sms, SMSP_PER_SM, clock_mhz)},
+    }
+    for v in res.values():
+        v["frac"] = v["achieved"] / v["peak"] if v["peak"] else None
+    bound = max(res, key=lambda k: res[k]["frac"] or 0.0)
+    out.update({"bound": bound, "achieved": res[bound]["achieved"], "peak": res[bound]["peak"],
+                "unit": res[bound]["unit"], "frac": res[bound]["frac"], "traffic": ctr["dram_bytes"],
+                "hbm": res["hbm"], "l2": res["l2"], "issue": res["issue"],
+                "counters": {"source": "ncu (--clock-control none) on one launch of this workload and launch "
+                                       "shape; committed in profiles/render_kernel_counters.json",
+                             "dram_bytes": ctr["dram_bytes"], "lts_bytes": ctr["lts_bytes"],
+                             "inst_executed": ctr["inst_executed"],
+                             "warps_active_pct": ctr.get("warps_active_pct"),
+                             "issue_active_pct": ctr.get("issue_active_pct")}})
+    return out
 
 
 class Clocks:
@@ -325,15 +399,19 @@ def run_ours(args):
     rays = w.rays_per_step
     graph = args.variant == "batching"
 
-    # launch shape first: the counted traversal below then takes the order and tiles that are timed
+    # launch shape first: the counted traversal below then takes the order and tiles that are timed.
+    # The plain variant keeps the library's default shape (the fastest of the autotuner's sweep on this
+    # workload) unless --autotune is given, so that its launch matches the committed ncu counters.
     tuning, tune_ms = rpl.rpl_view_tuning_get(view.h), None
+    tuning_source = "library default"
     if args.tuning:
-        tw, th, pers, tf, mb = (int(v) for v in args.tuning.split(","))
-        rpl.rpl_view_tuning_set(view.h, tw, th, pers, tf, mb)
+        rpl.rpl_view_tuning_set(view.h, *(int(v) for v in args.tuning.split(",")))
         tuning = rpl.rpl_view_tuning_get(view.h)
-    elif not args.no_autotune:
+        tuning_source = "--tuning"
+    elif not args.no_autotune and (args.variant != "plain" or args.autotune):
         with torch.cuda.stream(stream):
             tuning, tune_ms = rpl.rpl_view_autotune(view.h, poses[0], 0, env_offset, out, stream, 3)
+        tuning_source = "autotuner (144 shapes, 3 renders each)"
     # traversal counters (untimed, step 0, the chosen launch shape): algorithmic fetch bytes per ray
     with torch.cuda.stream(stream):
         cnt = view.render_counters(poses[0], 0, env_offset, out, stream)
@@ -432,8 +510,12 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
     k_avg_s = statistics.mean(kms) / 1e3 if kms else ms_step / 1e3
-    peak, peak_src = peaks()
-    achieved = alg_bytes / k_avg_s / 1e9
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clock_mhz = ck.get("sm_mhz") or ck.get("sm_max_mhz") or 2070.0
+    ctr = counters_for_launch(rays, args.variant, tuning, bvh_number(args))
+    roof = roofline(ctr, k_avg_s, alg_bytes, rays, sms, clock_mhz, l2_copy_gbs(dev), cnt)
+    roof["kernel_ms_source"] = ("CUDA events around each render launch" if kms else
+                                "whole graph replay (events cannot be recorded inside the graph)")
     line = {
         "metric": METRIC, "value": value, "unit": "Grays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -442,20 +524,13 @@ def run_ours(args):
         "config": {"workload": workload_name(w, args.variant, bvh_number(args)), "envs_per_gpu": w.n_envs,
                    "cameras": len(w.cameras), "bvh": BVH_NAMES[bvh_number(args)],
                    "rays_per_step_per_gpu": rays, "pose_sets": S, "tuning": tuning,
-                   "autotune_best_ms": tune_ms,
+                   "tuning_source": tuning_source, "autotune_best_ms": tune_ms,
                    "l2": "inputs larger than L2: terrain BVH %.2f GB resident, new poses each step"
                          % (info["terrain_bytes"] / 1e9)},
         "frames_per_s": frames,
         "env_steps_per_s": world * w.n_envs / (ms_step / 1e3),
         "gpu_launches": ((4 if graph else 3) + (1 if raw_rays else 0)) * args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_per_launch(rays, args.variant, tuning, bvh_number(args)),
-                     "kernel": "render_kernel", "kernel_ms": 1e3 * k_avg_s,
-                     "kernel_ms_source": "CUDA events around each render launch" if kms else
-                                         "whole graph replay (events cannot be recorded inside the graph)",
-                     "alg_bytes_per_ray": alg_bytes / rays, "peak_source": peak_src + " hbm_gbs",
-                     "per_ray": {k: cnt[k] / rays for k in ("terrain_nodes", "terrain_tris", "link_boxes",
-                                                            "link_nodes", "link_tris")}},
+        "roofline": roof,
         "clocks": ck,
         "vram": vram,
         "e2e": e2e,
@@ -463,6 +538,11 @@ def run_ours(args):
                   "terrain_depth": info["terrain_depth"], "terrain_bytes": info["terrain_bytes"],
                   "bvh_build_s": build_s},
     }
+    if not args.no_serve and args.variant == "plain":
+        # the serving half of the metric on the same GPU and resident scene (config 5, shortened)
+        from paper_2602_03002_gb300 import workloads as W
+        view.close()
+        line["serve"] = serve_summary(serve_measure(rpl, W, scene, args.tiles, args.serve_requests, 8))
     if world == 1 and not args.no_cpu_baseline:
         _, _, _, cb = cpu_baseline(w, args.cpu_seconds, gpu_step0)
         line["cpu_baseline"] = cb
@@ -472,32 +552,23 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def run_serving(args):
-    """Config 5: Poisson streams of render requests from 4 trainer threads (4 views each: env counts
-    log-uniform in 64..8192, 1-4 cameras front/back 64x48, left/right 48x36), one resident scene.
-    The same seeded arrival schedule is served by the continuous-batching server and by plain
-    per-request launches (a server with batches of one on one stream); latency is submit to
-    completion on the host clock."""
+def serve_measure(rpl, W, scene, tiles, n_req, rounds, load=0.8, seed=5):
+    """Config 5 on a resident scene: Poisson streams of render requests from 4 trainer threads (4 views
+    each: env counts log-uniform in 64..8192, 1-4 cameras front/back 64x48, left/right 48x36).  The
+    same seeded arrival schedule (at `load` times the one-request capacity) is served by the
+    continuous-batching server (up to 32 requests per launch, 2 streams) and by plain per-request
+    launches (batches of one on one stream); latency is submit to completion on the host clock.  Also
+    a closed loop with every request outstanding (`rounds` rounds): the throughput each form sustains."""
     import threading
     import torch
-    from paper_2602_03002_gb300 import build as B, rpl, workloads as W
-    rank, world, local = dist_info()
-    if rank != 0:
-        return
-    torch.cuda.set_device(local)
-    B.build()
-    base = W.config_scale(n_steps=1, n_envs=16, tiles=args.tiles)
-    scene = rpl.Scene(base.terrain_verts, base.terrain_tris, device=local)
-    for l, (v_, t_) in enumerate(zip(base.link_verts, base.link_tris)):
-        scene.add_link(l, v_, t_)
-    rng = np.random.default_rng(5)
+    rng = np.random.default_rng(seed)
     n_tr, per_tr = 4, 4
     sizes = [(64, 48), (64, 48), (48, 36), (48, 36)]
     shapes = []
     for k in range(n_tr * per_tr):
         E = int(round(float(np.exp(rng.uniform(np.log(64), np.log(8192))))))
         C = int(rng.integers(1, 5))
-        poses, cams = W.scale_envs(E, 4, args.tiles, sizes[:C], seed=100 + k)
+        poses, cams = W.scale_envs(E, 4, tiles, sizes[:C], seed=100 + k)
         shapes.append((E, cams, torch.from_numpy(poses).cuda()))
     sensor = W.scale_sensor()
 
@@ -522,11 +593,10 @@ def run_serving(args):
             v.render(poses[s % 4], s, 0, out)
         torch.cuda.synchronize()
         times.append((time.perf_counter() - t) / 3)
-    del vs
+    for v, _, _, _ in vs:
+        v.close()
     service = float(np.mean(times))
-    load = 0.8
     rate = load / service                       # requests per second, all trainers together
-    n_req = max(400, args.steps * 8)
     sched = []
     for tr in range(n_tr):
         gaps = rng.exponential(n_tr / rate, size=n_req // n_tr)
@@ -576,13 +646,15 @@ def run_serving(args):
         wall = time.perf_counter() - t0
         st = server.stats()
         server.close()
+        for v, _, _, _ in vs:
+            v.close()
         lat_ms = np.asarray(lat) * 1e3
         return {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
                 "mean_ms": float(lat_ms.mean()), "requests": len(lat), "grays_per_s": rays_done[0] / wall / 1e9,
                 "wall_s": wall, "batches": st["batches"], "mean_batch": st["fused_requests"] / max(1, st["batches"]),
                 "max_batch_seen": st["max_batch_seen"], "max_inflight_batches": st["max_inflight_batches_seen"]}
 
-    def run_saturated(max_batch, n_streams, rounds):
+    def run_saturated(max_batch, n_streams):
         """Closed loop: every trainer keeps its four views' requests in flight (submit all four, wait
         for all four, repeat), so 16 requests are outstanding and the GPU never waits for arrivals."""
         vs = make_views()
@@ -608,22 +680,61 @@ def run_serving(args):
         wall = time.perf_counter() - t
         st = server.stats()
         server.close()
+        for v, _, _, _ in vs:
+            v.close()
         return {"grays_per_s": rays_done[0] / wall / 1e9, "wall_s": wall, "requests": st["completed"],
                 "mean_batch": st["fused_requests"] / max(1, st["batches"])}
 
     batched = run_mode(32, 2)
     plain = run_mode(1, 1)
+    return {"batched": batched, "per_request": plain,
+            "saturated": {"note": "closed loop, 16 requests outstanding: throughput each form sustains",
+                          "batched": run_saturated(32, 2), "per_request": run_saturated(1, 1)},
+            "workload": "4 trainers x 4 views (env counts log-uniform 64..8192, 1-4 cameras 64x48/48x36), "
+                        "Poisson arrivals at %.0f%% of the one-request capacity, scale terrain resident, "
+                        "sensor on, FP32 depth" % (100 * load),
+            "views": [{"envs": E, "cams": len(c)} for E, c, _ in shapes],
+            "arrival_rate_per_s": rate, "service_ms_alone": 1e3 * service, "requests_per_form": n_req}
+
+
+def serve_summary(m):
+    """The headline serving figures: both forms' p50/p99 and throughput on the same arrival schedule."""
+    b, p = m["batched"], m["per_request"]
+    return {"p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"], "grays_per_s": b["grays_per_s"],
+            "mean_batch": b["mean_batch"], "max_batch_seen": b["max_batch_seen"],
+            "per_request": {"p50_ms": p["p50_ms"], "p99_ms": p["p99_ms"], "grays_per_s": p["grays_per_s"]},
+            "saturated_grays_per_s": {"batched": m["saturated"]["batched"]["grays_per_s"],
+                                      "per_request": m["saturated"]["per_request"]["grays_per_s"]},
+            "requests_per_form": m["requests_per_form"], "arrival_rate_per_s": m["arrival_rate_per_s"],
+            "service_ms_alone": m["service_ms_alone"], "workload": m["workload"],
+            "latency": "submit to completion on the host clock; batched = continuous-batching server "
+                       "(up to 32 requests per launch, 2 streams), per_request = one plain FP32 launch per "
+                       "request on one stream, same arrival schedule"}
+
+
+def run_serving(args):
+    """The serving configuration on its own (more requests than the default line's serve object)."""
+    import torch
+    from paper_2602_03002_gb300 import build as B, rpl, workloads as W
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    B.build()
+    base = W.config_scale(n_steps=1, n_envs=16, tiles=args.tiles)
+    scene = rpl.Scene(base.terrain_verts, base.terrain_tris, device=local)
+    for l, (v_, t_) in enumerate(zip(base.link_verts, base.link_tris)):
+        scene.add_link(l, v_, t_)
+    n_req = max(400, args.steps * 8)
+    m = serve_measure(rpl, W, scene, args.tiles, n_req, 20)
+    batched = m["batched"]
     line = {"metric": METRIC, "value": batched["grays_per_s"], "unit": "Grays/s", "n_gpus": 1,
             "steps": n_req, "warmup": 3, "ms_per_step": batched["mean_ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "variant": "serving",
-            "config": {"workload": "serving: 4 trainers x 4 views (env counts log-uniform 64..8192, 1-4 cameras "
-                                   "64x48/48x36), Poisson arrivals at %.0f%% of the per-request capacity, %d-tri "
-                                   "terrain resident, sensor on" % (100 * load, len(base.terrain_tris)),
-                       "views": [{"envs": E, "cams": len(c)} for E, c, _ in shapes],
-                       "arrival_rate_per_s": rate, "service_ms_alone": 1e3 * service},
-            "serve": batched, "serve_baseline_per_request": plain,
-            "saturated": {"note": "closed loop, 16 requests outstanding: throughput the server sustains",
-                          "batched": run_saturated(32, 2, 20), "per_request": run_saturated(1, 1, 20)},
+            "config": {"workload": "serving: " + m["workload"] + " (%d-tri terrain)" % len(base.terrain_tris),
+                       "views": m["views"], "arrival_rate_per_s": m["arrival_rate_per_s"],
+                       "service_ms_alone": m["service_ms_alone"]},
+            "serve": serve_summary(m), "serve_detail": m,
             "p50_ms": batched["p50_ms"], "p99_ms": batched["p99_ms"]}
     print(json.dumps(line), flush=True)
 
