@@ -534,7 +534,10 @@ def run_ours(args):
                          % (info["terrain_bytes"] / 1e9)},
         "frames_per_s": frames,
         "env_steps_per_s": world * w.n_envs / (ms_step / 1e3),
-        "gpu_launches": ((4 if graph else 3) + (1 if raw_rays else 0)) * args.steps,
+        # per step: prep, tile prep and render kernels, the env-order sort when the shape asks for it,
+        # the downsample kernel for downsampled cameras, the step advance of a graph replay
+        "gpu_launches": (3 + (1 if tuning.get("env_order") else 0) + (1 if graph else 0)
+                         + (1 if raw_rays else 0)) * args.steps,
         "roofline": roof,
         "clocks": ck,
         "vram": vram,
