@@ -416,7 +416,7 @@ def run_ours(args):
     elif not args.no_autotune and (args.variant == "batching" or args.autotune):
         with torch.cuda.stream(stream):
             tuning, tune_ms = rpl.rpl_view_autotune(view.h, poses[0], 0, env_offset, out, stream, 3)
-        tuning_source = "autotuner (144 shapes, 3 renders each)"
+        tuning_source = "autotuner (192 shapes, 3 renders each)"
     # traversal counters (untimed, step 0, the chosen launch shape): algorithmic fetch bytes per ray
     with torch.cuda.stream(stream):
         cnt = view.render_counters(poses[0], 0, env_offset, out, stream)

@@ -275,9 +275,9 @@ RPL_API rpl_status rpl_view_host_async(rpl_view_t view, int32_t enable);
  * block (a view renders on one stream at a time: its queue counters are shared by its renders);
  * terrain_first: query the terrain before the links (Alg. 1 queries
  * the bodies first; the depth is the same either way); min_blocks: 8 (up to 64 registers per
- * thread), 10 (up to 48) or 12 (up to 40) resident blocks of 128 threads per SM.  The shape never changes the
- * result, only the speed.  Default: 4x8, persistent 2 (per-SM queues), links first, 8, env_order 1,
- * chunk_envs 1. */
+ * thread), 9 (up to 56), 10 (up to 48) or 12 (up to 40) resident blocks of 128 threads per SM.  The
+ * shape never changes the result, only the speed.  Default: 4x8, persistent 2 (per-SM queues), links
+ * first, 9, env_order 1, chunk_envs 1. */
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t persistent;
@@ -294,9 +294,9 @@ RPL_API rpl_status rpl_view_tuning_set(rpl_view_t view, const rpl_tuning *tuning
 RPL_API rpl_status rpl_view_tuning_get(rpl_view_t view, rpl_tuning *tuning);
 
 /* Autotuner: renders `step` (same step rules as rpl_render; device buffers only) `reps` times
- * with each of 144 launch shapes (tile 8x4 / 4x8 / 16x2; persistent 0 / 1 / 2, each in env index
+ * with each of 192 launch shapes (tile 8x4 / 4x8 / 16x2; persistent 0 / 1 / 2, each in env index
  * or spatial order, the per-SM queues contiguous or dealt one env at a time; links or terrain
- * first; 8, 10 or 12 blocks per SM), times them with CUDA events on `stream`, keeps the fastest on the
+ * first; 8, 9, 10 or 12 blocks per SM), times them with CUDA events on `stream`, keeps the fastest on the
  * view and returns it with its mean time per render.  Synchronises; for setup, not the hot loop. */
 RPL_API rpl_status rpl_view_autotune(rpl_view_t view, const float *link_poses, int64_t step,
                                      int64_t env_offset, void *depth_out, void *stream, int32_t reps,

@@ -1283,7 +1283,7 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
 }
 
 // kMinBlocks caps registers so that many blocks of 128 threads stay resident per SM (8 -> 64
-// registers, 10 -> 48, 12 -> 40).  With p.persistent the grid holds only as many blocks as fit on
+// registers, 9 -> 56, 10 -> 48, 12 -> 40).  With p.persistent the grid holds only as many blocks as fit on
 // the device at once and each warp walks the tiles with a grid stride; otherwise one warp per tile.
 // kQueued (p.queues set, same grid as persistent): warps take tiles from per-SM queues instead.
 // kTileInfo = false serves callers that run no tile prep (p.tile_info null).
@@ -1570,7 +1570,7 @@ __global__ void __launch_bounds__(1024) env_order_kernel(const uint32_t *__restr
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     for (int i = t; i < kOrderBuckets; i += 1024) h[i] = 0u;
     __syncthreads();
-    for (int e = t; e < E; e += 1024) atomicAdd(&h[__ldg(key + e) & (kOrderBuckets - 1)], 1u);
+    for (int64_t e = t; e < E; e += 1024) atomicAdd(&h[__ldg(key + e) & (kOrderBuckets - 1)], 1u);
     __syncthreads();
     // exclusive scan: each thread owns kPer consecutive buckets
     uint32_t v[kPer], sum = 0;
@@ -1604,7 +1604,7 @@ __global__ void __launch_bounds__(1024) env_order_kernel(const uint32_t *__restr
         run += v[k];
     }
     __syncthreads();
-    for (int e = t; e < E; e += 1024) order[atomicAdd(&h[__ldg(key + e) & (kOrderBuckets - 1)], 1u)] = e;
+    for (int64_t e = t; e < E; e += 1024) order[atomicAdd(&h[__ldg(key + e) & (kOrderBuckets - 1)], 1u)] = (int32_t)e;
 }
 
 }  // namespace
@@ -1630,12 +1630,16 @@ void launch_kind(const RenderParams &p, bool count, int min_blocks, unsigned g, 
         render_kernel<false, kKind, 12, true, true><<<g, 128, 0, s>>>(p);
     else if (p.queues && min_blocks == 10)
         render_kernel<false, kKind, 10, true, true><<<g, 128, 0, s>>>(p);
+    else if (p.queues && min_blocks == 9)
+        render_kernel<false, kKind, 9, true, true><<<g, 128, 0, s>>>(p);
     else if (p.queues)
         render_kernel<false, kKind, 8, true, true><<<g, 128, 0, s>>>(p);
     else if (min_blocks == 12)
         render_kernel<false, kKind, 12><<<g, 128, 0, s>>>(p);
     else if (min_blocks == 10)
         render_kernel<false, kKind, 10><<<g, 128, 0, s>>>(p);
+    else if (min_blocks == 9)
+        render_kernel<false, kKind, 9><<<g, 128, 0, s>>>(p);
     else
         render_kernel<false, kKind, 8><<<g, 128, 0, s>>>(p);
 }
@@ -1664,7 +1668,7 @@ cudaError_t launch_tile_prep(const RenderParams &p, cudaStream_t s) {
 cudaError_t launch_render(const RenderParams &p, bool count, cudaStream_t s) {
     const int64_t warps = (int64_t)p.E * p.tiles_per_env;
     if (warps == 0) return cudaSuccess;
-    const int min_blocks = p.min_blocks == 12 ? 12 : (p.min_blocks == 10 ? 10 : 8);
+    const int min_blocks = p.min_blocks == 12 ? 12 : p.min_blocks == 10 ? 10 : p.min_blocks == 9 ? 9 : 8;
     int64_t blocks = (warps + 3) / 4;
     if (p.persistent || (p.queues && p.tile_info && !count)) {
         int dev = 0, sms = 0;

@@ -70,7 +70,7 @@ struct Tuning {
                              // contiguous queue per SM, warps take tiles from their SM's queue and
                              // then from the fullest other queue
     int32_t terrain_first;   // query the terrain before the links
-    int32_t min_blocks;      // 8 (64 registers) or 12 (40 registers) blocks of 128 per SM
+    int32_t min_blocks;      // 8, 9, 10 or 12 blocks of 128 per SM (64, 56, 48 or 40 registers)
     int32_t env_order;       // 1: tiles are processed env by env in the spatial order of the envs
                              // (sorted by position each render), 0: in env index order
     int32_t chunk_envs;      // persistent == 2 only: 0 = one contiguous range of tiles per queue; > 0 =

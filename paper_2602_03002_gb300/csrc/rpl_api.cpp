@@ -220,9 +220,9 @@ struct rpl_view {
     cudaEvent_t ev[2 * kTimingSlots] = {};
     int64_t n_timed = 0;
     // launch shape of the render kernel: 4x8 tiles, per-SM tile queues dealt one env at a time in the
-    // spatial order of the envs, links first, 8 blocks per SM (the fastest shape of the autotuner's
+    // spatial order of the envs, links first, 9 blocks per SM (the fastest shape of the autotuner's
     // sweep on the 4096-env scale workload)
-    Tuning tune{2, 2, 0, 8, 1, 1};
+    Tuning tune{2, 2, 0, 9, 1, 1};
     // graph replay (rpl_render_graph): device step counter, captured graph and what it was captured for
     DevBuf d_step;
     int64_t dev_step_next = INT64_MIN; // value the device counter holds before the next replay
@@ -1267,7 +1267,8 @@ RPL_API rpl_status rpl_view_kernel_ms(rpl_view_t v, float *ms, int32_t max_n, in
 
 static bool tuning_from(const rpl_tuning *t, Tuning *out) {
     const int lg = t->tile_w == 4 ? 2 : t->tile_w == 8 ? 3 : t->tile_w == 16 ? 4 : -1;
-    if (lg < 0 || t->tile_w * t->tile_h != 32 || (t->min_blocks != 8 && t->min_blocks != 10 && t->min_blocks != 12))
+    if (lg < 0 || t->tile_w * t->tile_h != 32 ||
+        (t->min_blocks != 8 && t->min_blocks != 9 && t->min_blocks != 10 && t->min_blocks != 12))
         return false;
     out->tile_w_log2 = lg;
     if (t->persistent < 0 || t->persistent > 2 || t->env_order < 0 || t->env_order > 1 || t->chunk_envs < 0 ||
@@ -1296,7 +1297,7 @@ RPL_API rpl_status rpl_view_tuning_set(rpl_view_t v, const rpl_tuning *t) {
     Tuning n;
     if (!tuning_from(t, &n))
         return fail(RPL_ERR_INVALID_ARG, "rpl_view_tuning_set: tile must be 4x8, 8x4 or 16x2, persistent 0, 1 or 2, "
-                    "min_blocks 8, 10 or 12, env_order 0 or 1 and chunk_envs 0..2^20");
+                    "min_blocks 8, 9, 10 or 12, env_order 0 or 1 and chunk_envs 0..2^20");
     v->tune = n;
     return RPL_OK;
 }
@@ -1344,8 +1345,9 @@ RPL_API rpl_status rpl_view_autotune(rpl_view_t v, const float *poses, int64_t s
     for (int ti = 0; ti < 3 && st == RPL_OK; ++ti)
         for (int sc = 0; sc < 8 && st == RPL_OK; ++sc)
             for (int tf = 0; tf < 2 && st == RPL_OK; ++tf)
-                for (int mb = 8; mb <= 12 && st == RPL_OK; mb += 2) {
-                    v->tune = Tuning{tiles[ti], sched[sc][0], tf, mb, sched[sc][1], sched[sc][2]};
+                for (int mi = 0; mi < 4 && st == RPL_OK; ++mi) {
+                    const int mbs[4] = {8, 9, 10, 12};
+                    v->tune = Tuning{tiles[ti], sched[sc][0], tf, mbs[mi], sched[sc][1], sched[sc][2]};
                     st = enqueue(v, poses, step, env_offset, out, cs, false, nullptr);   // warm-up
                     if (st != RPL_OK) break;
                     cudaEventRecord(a, cs);

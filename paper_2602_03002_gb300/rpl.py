@@ -371,7 +371,7 @@ def rpl_static_scratch_status(scene: int, stream=None):
 
 
 def rpl_view_tuning_set(view: int, tile_w: int = 4, tile_h: int = 8, persistent: int = 2, terrain_first: int = 0,
-                        min_blocks: int = 8, env_order: int = 1, chunk_envs: int = 1):
+                        min_blocks: int = 9, env_order: int = 1, chunk_envs: int = 1):
     t = rpl_tuning(tile_w, tile_h, persistent, terrain_first, min_blocks, env_order, chunk_envs)
     _check(lib().rpl_view_tuning_set(view, ctypes.byref(t)))
 
@@ -383,7 +383,7 @@ def rpl_view_tuning_get(view: int) -> dict:
 
 
 def rpl_view_autotune(view: int, poses, step: int, env_offset: int, out, stream=None, reps: int = 3):
-    """Times the 144 launch shapes, keeps the fastest on the view; returns (tuning dict, ms per render)."""
+    """Times the 192 launch shapes, keeps the fastest on the view; returns (tuning dict, ms per render)."""
     t = rpl_tuning()
     ms = ctypes.c_float()
     _check(lib().rpl_view_autotune(view, _ptr(poses), int(step), int(env_offset), _ptr(out), _stream_handle(stream),

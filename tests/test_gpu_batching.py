@@ -18,18 +18,18 @@ from paper_2602_03002_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 SHAPES = [dict(tile_w=tw, tile_h=32 // tw, persistent=p, terrain_first=tf, min_blocks=mb, env_order=0, chunk_envs=0)
-          for tw, p, tf, mb in itertools.product((8, 4, 16), (0, 1, 2), (0, 1), (8, 10, 12))]
+          for tw, p, tf, mb in itertools.product((8, 4, 16), (0, 1, 2), (0, 1), (8, 9, 10, 12))]
 # the spatial env order with each scheduling, and per-SM queues dealt in chunks of 1, 3 and 7 envs
 SHAPES += [dict(tile_w=tw, tile_h=32 // tw, persistent=p, terrain_first=0, min_blocks=8, env_order=o, chunk_envs=k)
            for tw, p, o, k in itertools.product((8, 4), (0, 1, 2), (0, 1), (0, 1, 3, 7)) if (o or k) and (p == 2 or k == 0)]
 
 
-# the autotuner's 144 shapes
+# the autotuner's 192 shapes
 AUTOTUNE_SHAPES = [dict(tile_w=tw, tile_h=32 // tw, persistent=p, terrain_first=tf, min_blocks=mb, env_order=o,
                         chunk_envs=k)
                    for tw, (p, o, k), tf, mb in itertools.product(
                        (8, 4, 16), ((0, 0, 0), (0, 1, 0), (1, 0, 0), (1, 1, 0), (2, 0, 0), (2, 1, 0), (2, 0, 1), (2, 1, 1)),
-                       (0, 1), (8, 10, 12))]
+                       (0, 1), (8, 9, 10, 12))]
 
 
 def _ragged(w):
@@ -104,7 +104,7 @@ def test_autotune_picks_a_shape_and_keeps_results(cuda, rpl_lib):
     ref = view.render(poses, 0).clone()
     out = torch.empty_like(ref)
     best, ms = rpl_lib.rpl_view_autotune(view.h, poses, 0, 0, out, None, 2)
-    assert best in AUTOTUNE_SHAPES and ms > 0 and len(AUTOTUNE_SHAPES) == 144
+    assert best in AUTOTUNE_SHAPES and ms > 0 and len(AUTOTUNE_SHAPES) == 192
     assert rpl_lib.rpl_view_tuning_get(view.h) == best
     assert torch.equal(view.render(poses, 0), ref)
 
