@@ -195,3 +195,30 @@ def test_per_sm_queues_with_fewer_tiles_than_queues(cuda, rpl_lib, n_envs, size)
             view.render(poses[s], s, 0, out)
             assert torch.equal(out, ref[s]), (tw, s)
     view.sync()
+
+
+def test_spatial_env_order_with_coincident_and_outside_envs(cuda, rpl_lib):
+    """The spatial processing order buckets envs by position: envs that share one position (one
+    bucket, arbitrary order inside it) and envs far outside the terrain (clamped to the edge cells)
+    must render the same frames in env index order and in spatial order, contiguous or dealt in
+    chunks."""
+    torch = cuda
+    w = W.config_small(n_steps=2, n_envs=12)
+    poses = w.poses.copy()
+    poses[:, 1:6, :, :2] += poses[:, :1, :1, :2] - poses[:, 1:6, :1, :2]      # envs 1-5 stand where env 0 does
+    poses[:, 9:12, :, 0] += 1.0e4                                           # envs 9-11 far outside the terrain
+    sen = W.Sensor(sigma_abs=0.01, p_drop=0.05, max_latency=1, seed=(7, 8))
+    scene = rpl_lib.Scene.from_workload(w)
+    view = rpl_lib.View(scene, w.n_envs, w.n_links)
+    view.set_cameras(w.cameras)
+    view.set_sensor(sen)
+    pt = torch.from_numpy(poses).cuda()
+    rpl_lib.rpl_view_tuning_set(view.h, tile_w=4, tile_h=8, persistent=2, env_order=0, chunk_envs=0)
+    ref = [view.render(pt[s], s).clone() for s in range(2)]
+    assert bool((ref[1][9:] == 3.0).any())                                  # the outside envs see nothing
+    for order, chunk, pers in ((1, 0, 2), (1, 1, 2), (1, 5, 2), (1, 0, 0), (1, 0, 1)):
+        rpl_lib.rpl_view_tuning_set(view.h, tile_w=4, tile_h=8, persistent=pers, env_order=order, chunk_envs=chunk)
+        view.reset(None, 0)
+        for s in range(2):
+            assert torch.equal(view.render(pt[s], s), ref[s]), (order, chunk, pers, s)
+    view.sync()
