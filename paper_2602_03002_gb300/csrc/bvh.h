@@ -24,7 +24,8 @@ static_assert(sizeof(BvhNode) == 64, "node is 64 bytes");
 
 struct alignas(16) BvhTri {
     float v0x, v0y, v0z, id;    // id: original triangle index (bit pattern of an int32)
-    float v1x, v1y, v1z, pad1;
+    float v1x, v1y, v1z, pad1;  // pad1: 1 on the device when this triangle (A, B, C) and the next
+                                // one (A, C, D) form a pair sharing the edge A-C (a quad), else 0
     float v2x, v2y, v2z, pad2;
 };
 static_assert(sizeof(BvhTri) == 48, "triangle is 48 bytes");

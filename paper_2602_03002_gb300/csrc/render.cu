@@ -626,6 +626,30 @@ __device__ __forceinline__ float3 shear_vertex(const Ray &r, float vx, float vy,
     return make_float3(fmaf(-r.Sx, pz, comp(a, kx)), fmaf(-r.Sy, pz, comp(a, ky)), r.Sz * pz);
 }
 
+// The rest of the watertight test once the edge functions U, V, W of the sheared triangle are known
+// (az, bz, cz: its sheared vertices' z): inside test (closed, two-sided), determinant, hit
+// distance.  The arithmetic is spelled out with round-to-nearest intrinsics, so every caller gets
+// the same bits for the same inputs.
+__device__ __forceinline__ bool tri_finish(float U, float V, float W, float az, float bz, float cz, float &tmax) {
+    const bool has_neg = (U < 0.f) || (V < 0.f) || (W < 0.f);
+    const bool has_pos = (U > 0.f) || (V > 0.f) || (W > 0.f);
+    if (has_neg && has_pos) return false;
+    const float det = __fadd_rn(__fadd_rn(U, V), W);
+    if (det == 0.f) return false;
+    const float T = __fmaf_rn(W, cz, __fmaf_rn(V, bz, __fmul_rn(U, az)));
+    const float td = __fmul_rn(tmax, det);
+    if (det > 0.f ? (T <= 0.f || T > td) : (T >= 0.f || T < td)) return false;
+    const float t = __fdiv_rn(T, det);
+    if (!(t > 0.f && t < tmax)) return false;
+    tmax = t;
+    return true;
+}
+
+// 2D edge function of the sheared vertices P, Q, evaluated without contraction.
+__device__ __forceinline__ float edge_fn(const float3 &P, const float3 &Q) {
+    return __fsub_rn(__fmul_rn(P.x, Q.y), __fmul_rn(P.y, Q.x));
+}
+
 // Two-sided, closed watertight test.  The 2D edge functions are evaluated without contraction, so a
 // shared edge yields exactly negated values in its two triangles and no ray slips between them.
 template <bool kSplit>
@@ -634,20 +658,24 @@ __device__ __forceinline__ bool tri_hit(const Ray &r, const float4 &v0, const fl
     const float3 A = shear_vertex<kSplit>(r, v0.x, v0.y, v0.z);
     const float3 B = shear_vertex<kSplit>(r, v1.x, v1.y, v1.z);
     const float3 C = shear_vertex<kSplit>(r, v2.x, v2.y, v2.z);
-    const float U = __fsub_rn(__fmul_rn(C.x, B.y), __fmul_rn(C.y, B.x));
-    const float V = __fsub_rn(__fmul_rn(A.x, C.y), __fmul_rn(A.y, C.x));
-    const float W = __fsub_rn(__fmul_rn(B.x, A.y), __fmul_rn(B.y, A.x));
-    const bool has_neg = (U < 0.f) || (V < 0.f) || (W < 0.f);
-    const bool has_pos = (U > 0.f) || (V > 0.f) || (W > 0.f);
-    if (has_neg && has_pos) return false;
-    const float det = U + V + W;
-    if (det == 0.f) return false;
-    const float T = U * A.z + V * B.z + W * C.z;
-    if (det > 0.f ? (T <= 0.f || T > tmax * det) : (T >= 0.f || T < tmax * det)) return false;
-    const float t = __fdiv_rn(T, det);
-    if (!(t > 0.f && t < tmax)) return false;
-    tmax = t;
-    return true;
+    return tri_finish(edge_fn(C, B), edge_fn(A, C), edge_fn(B, A), A.z, B.z, C.z, tmax);
+}
+
+// The pair (A, B, C), (A, C, D) of a quad leaf: four vertices sheared instead of six.  The second
+// triangle's edge function of C-A is edge_fn(C, A), which equals -edge_fn(A, C) exactly (the same
+// two rounded products, subtracted the other way round; only the sign of a zero can differ, and it
+// changes no decision).  So this gives the bits of tri_hit on each triangle in turn.
+template <bool kSplit>
+__device__ __forceinline__ bool quad_hit(const Ray &r, const float4 &v0, const float4 &v1, const float4 &v2,
+                                         const float4 &v3, float &tmax) {
+    const float3 A = shear_vertex<kSplit>(r, v0.x, v0.y, v0.z);
+    const float3 B = shear_vertex<kSplit>(r, v1.x, v1.y, v1.z);
+    const float3 C = shear_vertex<kSplit>(r, v2.x, v2.y, v2.z);
+    const float3 D = shear_vertex<kSplit>(r, v3.x, v3.y, v3.z);
+    const float eAC = edge_fn(A, C);
+    bool h = tri_finish(edge_fn(C, B), eAC, edge_fn(B, A), A.z, B.z, C.z, tmax);
+    h |= tri_finish(edge_fn(D, C), edge_fn(A, D), -eAC, A.z, C.z, D.z, tmax);
+    return h;
 }
 
 struct Counts {
@@ -663,8 +691,22 @@ __device__ __forceinline__ void leaf(const float4 *__restrict__ tris, int first,
         return;
     }
 #endif
+    int i = first;
+    if (count == 2) {
+        const float4 a = __ldg(tris + 3 * i), b = __ldg(tris + 3 * i + 1), c = __ldg(tris + 3 * i + 2);
+        if (b.w != 0.f) {
+            // a quad: the second triangle is (a, c, d); only its last vertex is loaded
+            const float4 d = __ldg(tris + 3 * i + 5);
+            if (kCount) cnt.tris += 2;
+            hit |= quad_hit<kSplit>(r, a, b, c, d, tmax);
+            return;
+        }
+        if (kCount) ++cnt.tris;
+        hit |= tri_hit<kSplit>(r, a, b, c, tmax);
+        ++i;
+    }
 #pragma unroll 1
-    for (int i = first; i < first + count; ++i) {
+    for (; i < first + count; ++i) {
         const float4 a = __ldg(tris + 3 * i), b = __ldg(tris + 3 * i + 1), c = __ldg(tris + 3 * i + 2);
         if (kCount) ++cnt.tris;
         hit |= tri_hit<kSplit>(r, a, b, c, tmax);

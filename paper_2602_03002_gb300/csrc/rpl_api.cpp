@@ -144,6 +144,79 @@ void encode_for_device(std::vector<BvhNode> &nodes) {
     }
 }
 
+// Two-triangle leaves whose triangles share an edge (a grid cell split along its diagonal, a quad
+// face of a link mesh) are stored so that the first triangle is (A, B, C) and the second (A, C, D),
+// each a cyclic rotation of its input triangle (so its orientation is kept), and the first
+// triangle's v1.w (otherwise 0) is set to 1.  The binary traversal then tests the pair from four
+// vertices (the shared edge's function is the first triangle's negated, exactly); every other
+// reader tests the rotated triangles one by one.  nodes: host layout (leaf child ~first, count).
+// Returns the number of pairs.
+int64_t pair_quad_leaves(const std::vector<BvhNode> &nodes, std::vector<BvhTri> &tris) {
+    auto vert = [](const BvhTri &t, int k, float out[3]) {
+        const float *p = &t.v0x + 4 * k;
+        out[0] = p[0];
+        out[1] = p[1];
+        out[2] = p[2];
+    };
+    auto same = [](const float a[3], const float b[3]) { return a[0] == b[0] && a[1] == b[1] && a[2] == b[2]; };
+    auto put = [](BvhTri &t, int k, const float v[3]) {
+        float *p = &t.v0x + 4 * k;
+        p[0] = v[0];
+        p[1] = v[1];
+        p[2] = v[2];
+    };
+    int64_t pairs = 0;
+    for (const BvhNode &n : nodes) {
+        const int32_t ch[2] = {n.child0, n.child1}, cn[2] = {n.cnt0, n.cnt1};
+        for (int k = 0; k < 2; ++k) {
+            if (ch[k] >= 0 || cn[k] != 2) continue;
+            const int64_t first = ~(int64_t)ch[k];
+            if (first < 0 || first + 1 >= (int64_t)tris.size()) continue;
+            BvhTri &t0 = tris[(size_t)first], &t1 = tris[(size_t)first + 1];
+            float p[3][3], q[3][3];
+            for (int i = 0; i < 3; ++i) {
+                vert(t0, i, p[i]);
+                vert(t1, i, q[i]);
+            }
+            // the vertex of each triangle that the other does not have
+            int u = -1, w = -1, shared = 0;
+            for (int i = 0; i < 3; ++i) {
+                bool in_q = false, in_p = false;
+                for (int j = 0; j < 3; ++j) {
+                    in_q |= same(p[i], q[j]);
+                    in_p |= same(q[i], p[j]);
+                }
+                if (in_q) ++shared;
+                else u = i;
+                if (!in_p) w = i;
+            }
+            if (shared != 2 || u < 0 || w < 0) continue;
+            // first triangle: (A, B, C) with B its own vertex; second: (A, C, D) with D its own vertex
+            const int s0 = (u + 2) % 3, s1 = (w + 1) % 3;
+            float A[3], B[3], C[3], A1[3], C1[3], D[3];
+            for (int a = 0; a < 3; ++a) {
+                A[a] = p[s0][a];
+                B[a] = p[(s0 + 1) % 3][a];
+                C[a] = p[(s0 + 2) % 3][a];
+                A1[a] = q[s1][a];
+                C1[a] = q[(s1 + 1) % 3][a];
+                D[a] = q[(s1 + 2) % 3][a];
+            }
+            if (!same(A, A1) || !same(C, C1)) continue;   // the two are not oriented alike
+            put(t0, 0, A);
+            put(t0, 1, B);
+            put(t0, 2, C);
+            put(t1, 0, A1);
+            put(t1, 1, C1);
+            put(t1, 2, D);
+            t0.pad1 = 1.0f;
+            t1.pad1 = 0.0f;
+            ++pairs;
+        }
+    }
+    return pairs;
+}
+
 void quat_normalise(const float in[4], float out[4]) {
     double n = std::sqrt((double)in[0] * in[0] + (double)in[1] * in[1] + (double)in[2] * in[2] +
                          (double)in[3] * in[3]);
@@ -308,6 +381,7 @@ RPL_API rpl_status rpl_scene_create(const float *verts, int64_t n_verts, const i
             delete s;
             return fail(RPL_ERR_CAPACITY, "rpl_scene_create: BVH depth %d exceeds %d", bvh.depth, kStackDepth);
         }
+        pair_quad_leaves(bvh.nodes, bvh.tris);   // before any collapse: every layout tests the same triangles
         const void *node_src = bvh.nodes.data();
         size_t node_bytes = bvh.nodes.size() * sizeof(BvhNode);
         const std::vector<BvhTri> *tri_src = &bvh.tris;
@@ -417,6 +491,7 @@ static rpl_status freeze(rpl_scene *s) {
     }
     // leaf references carry (first triangle << 3) in 31 bits during traversal
     if (tris.size() >= (size_t)0x0FFFFFFF) return fail(RPL_ERR_CAPACITY, "the link meshes hold too many triangles");
+    pair_quad_leaves(nodes, tris);
     encode_for_device(nodes);
     if (nodes.empty()) nodes.push_back(BvhNode{});
     if (tris.empty()) tris.push_back(BvhTri{});
