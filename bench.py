@@ -400,6 +400,8 @@ def run_ours(args):
     stream = torch.cuda.Stream(dev)
     poses = torch.from_numpy(w.poses).to(f"cuda:{dev}")
     out = view.out_tensor(torch.device("cuda", dev))
+    # poses and out come from the default stream's memory pool; the side stream waits for that stream
+    stream.wait_stream(torch.cuda.current_stream(dev))
     rays = w.rays_per_step
     graph = args.variant == "batching"
 

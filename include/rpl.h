@@ -355,8 +355,13 @@ RPL_API rpl_status rpl_server_create(rpl_scene_t scene, const rpl_server_opts *o
  * for its first request) into depth_out; link_poses and depth_out are host (staged through the
  * server's budget) or device memory; they and the view must stay valid (not destroyed) until the
  * request completes: rpl_server_wait returned for it, or, for a cancelled request, the server was
- * destroyed.  While a view has requests in a server it must not be rendered by other calls.  *ticket identifies the
- * request.  Errors: INVALID_ARG, CAPACITY (the request's staging exceeds the whole budget). */
+ * destroyed.  While a view has requests in a server it must not be rendered by other calls.  The
+ * request runs after all work queued on the legacy default stream (cudaStreamLegacy, PyTorch's
+ * default stream) before this call: the server records an event there and its launch waits for it.
+ * Work on other streams that writes the poses or still uses depth_out's memory must be finished (or
+ * ordered before that stream point) by the caller.  *ticket identifies the request.  Errors:
+ * INVALID_ARG, CAPACITY (the request's staging exceeds the whole budget), CUDA (the event could not
+ * be recorded, e.g. during a global-mode stream capture). */
 RPL_API rpl_status rpl_server_submit(rpl_server_t server, rpl_view_t view, const float *link_poses, int64_t step,
                                      int64_t env_offset, void *depth_out, uint64_t *ticket);
 

@@ -11,6 +11,10 @@
 // buffers are on the device completes as soon as its own tiles are done: the kernel counts them off
 // and raises a flag in host-mapped memory that the worker polls, so a small request fused with a
 // large one does not wait for the large one.
+// The slots' streams are non-blocking, so at submit time the server records an event on the legacy
+// default stream and the request's launch waits for it: the request sees the poses and output
+// memory as work already queued on that stream left them (a producer kernel, a caching allocator
+// handing the memory out again).
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -102,6 +106,7 @@ struct Request {
     bool done = false, cancelled = false;
     bool early = false;   // completes by its own flag inside the fused launch
     bool waiting = false; // a thread is blocked in rpl_server_wait on it (it then owns the deletion)
+    cudaEvent_t ready = nullptr;   // recorded on the legacy default stream at submit (borrowed from the pool)
 };
 
 struct Slot {
@@ -141,19 +146,55 @@ struct rpl_server {
     rpl_server_stats stats{};
     bool registered = false;   // counted as a user of the scene
     std::thread worker;
+    std::mutex ev_mu;                     // guards the event pool (taken without mu)
+    std::vector<cudaEvent_t> ev_all, ev_free;
 };
 
 namespace {
+
+// Borrows an event from the server's pool (creating one if the pool is empty); the caller has set
+// the server's device.
+cudaError_t take_event(rpl_server *sv, cudaEvent_t *ev) {
+    std::lock_guard<std::mutex> lk(sv->ev_mu);
+    if (!sv->ev_free.empty()) {
+        *ev = sv->ev_free.back();
+        sv->ev_free.pop_back();
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) sv->ev_all.push_back(*ev);
+    return e;
+}
+
+// Returns a request's event to the pool once a wait on it has been queued (a later record does not
+// change what that wait waits for).
+void give_event(rpl_server *sv, Request *r) {
+    if (!r->ready) return;
+    std::lock_guard<std::mutex> lk(sv->ev_mu);
+    sv->ev_free.push_back(r->ready);
+    r->ready = nullptr;
+}
 
 // Fills slot s with the admitted batch and launches it (called without the server lock).
 void launch_batch(rpl_server *sv, Slot &s) {
     nvtxRangePushA("rpl_server_batch");
     cudaStream_t st = s.stream;
     const int n = (int)s.reqs.size();
+    for (int i = 0; i < n; ++i) {   // after the work queued on the legacy default stream before submit
+        Request *r = s.reqs[i];
+        if (!r->ready) continue;
+        const cudaError_t e = cudaStreamWaitEvent(st, r->ready, 0);
+        give_event(sv, r);
+        if (e != cudaSuccess) {
+            r->status = RPL_ERR_CUDA;
+            r->err = cudaGetErrorString(e);
+        }
+    }
     std::vector<RenderParams> prm(n);
     std::vector<int64_t> tiles(n, 0);
     for (int i = 0; i < n; ++i) {
         Request *r = s.reqs[i];
+        if (r->status != RPL_OK) continue;
         const float *pd = r->poses_host ? reinterpret_cast<const float *>(sv->arena_dev + r->pose_off) : r->poses;
         void *od = r->out_host ? (void *)(sv->arena_dev + r->out_off) : r->out;
         if (r->poses_host) {
@@ -439,10 +480,21 @@ RPL_API rpl_status rpl_server_submit(rpl_server_t sv, rpl_view_t view, const flo
         cudaSetDevice(sv->device);
         r->poses_host = view_envs(view) > 0 && !pointer_on_device(poses, sv->device);
         r->out_host = view_envs(view) > 0 && !pointer_on_device(out, sv->device);
+        cudaError_t e = cudaSuccess;
+        if (view_envs(view) > 0) {
+            e = take_event(sv, &r->ready);
+            if (e == cudaSuccess) e = cudaEventRecord(r->ready, cudaStreamLegacy);
+        }
         if (prev >= 0) cudaSetDevice(prev);
+        if (e != cudaSuccess) {
+            give_event(sv, r);
+            delete r;
+            return server_fail(RPL_ERR_CUDA, std::string("rpl_server_submit: ") + cudaGetErrorString(e));
+        }
     }
     const size_t staging = (r->poses_host ? round_up(r->pose_bytes) : 0) + (r->out_host ? round_up(r->out_bytes) : 0);
     if (staging > (size_t)sv->opts.staging_bytes) {
+        give_event(sv, r);
         delete r;
         return server_fail(RPL_ERR_CAPACITY, "rpl_server_submit: the request's host-buffer staging exceeds the "
                                              "server's whole staging budget");
@@ -451,6 +503,7 @@ RPL_API rpl_status rpl_server_submit(rpl_server_t sv, rpl_view_t view, const flo
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         if (sv->stop) {
+            give_event(sv, r);
             delete r;
             return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_submit: the server is stopping");
         }
@@ -458,6 +511,7 @@ RPL_API rpl_status rpl_server_submit(rpl_server_t sv, rpl_view_t view, const flo
         const bool order_ok = it != sv->last_submitted.end() ? (step == it->second || step == it->second + 1)
                                                              : view_step_allowed(view, step);
         if (!order_ok) {
+            give_event(sv, r);
             delete r;
             return server_fail(RPL_ERR_INVALID_ARG, "rpl_server_submit: a view's steps must advance by 0 or 1");
         }
@@ -560,6 +614,7 @@ RPL_API void rpl_server_destroy(rpl_server_t sv) {
     }
     if (sv->arena_dev) cudaFree(sv->arena_dev);
     for (auto &kv : sv->tickets) delete kv.second;
+    for (cudaEvent_t ev : sv->ev_all) cudaEventDestroy(ev);
     if (prev >= 0) cudaSetDevice(prev);
     rpl_scene *scene = sv->registered ? sv->scene : nullptr;
     delete sv;

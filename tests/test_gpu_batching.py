@@ -77,6 +77,9 @@ def test_graph_replay_continues_the_sensor_history(cuda, rpl_lib):
     stream = torch.cuda.Stream()
     pose_buf = torch.empty_like(poses[0])
     out = b.out_tensor()
+    # the side stream must wait for the default stream: the caching allocator may have given pose_buf
+    # and out memory that the direct renders' pending work on the default stream still uses
+    stream.wait_stream(torch.cuda.current_stream())
     got = []
     with torch.cuda.stream(stream):
         for s in range(6):

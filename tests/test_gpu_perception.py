@@ -119,6 +119,8 @@ def test_graph_replay_of_a_downsampled_view(cuda, rpl_lib):
     stream = torch.cuda.Stream()
     pose_buf = torch.empty_like(poses[0])
     out = b.out_tensor()
+    # the side stream waits for the default stream's pending work on memory the allocator may reuse
+    stream.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(stream):
         for s in range(4):
             pose_buf.copy_(poses[s])

@@ -91,6 +91,37 @@ def test_results_alone_equal_results_in_the_mix(cuda, rpl_lib):
     assert st["completed"] == st["submitted"] == 40 and st["failed"] == 0
 
 
+def test_request_runs_after_work_queued_on_the_default_stream(cuda, rpl_lib):
+    """The server's streams are non-blocking, so a request must be ordered after what the caller
+    queued on the default stream before submitting: here a ~20 ms sleep kernel, then the write of
+    the right poses over wrong ones and a fill of the output.  Rendered before that work, the request
+    would see the wrong poses, or its depth would be overwritten by the fill."""
+    torch = cuda
+    w = _workload()
+    scene = rpl_lib.Scene.from_workload(w)
+    (v, poses, E, C), = _views(rpl_lib, torch, w, scene, [(16, 4)])
+    alone = [v.render(poses[s], s, 0).clone() for s in range(3)]
+    torch.cuda.synchronize()
+    (v, poses, E, C), = _views(rpl_lib, torch, w, scene, [(16, 4)])
+    server = rpl_lib.Server(scene, max_batch=4, n_streams=2)
+    try:
+        for s in range(3):
+            src = poses[(s + 1) % 3].clone()            # wrong poses, written before the sleep
+            out = v.out_tensor()
+            out.fill_(-5.0)
+            torch.cuda.synchronize()
+            torch.cuda._sleep(40_000_000)               # bounded spin on the default stream
+            src.copy_(poses[s])
+            out.fill_(-7.0)
+            tk = server.submit(v, src, s, out)
+            server.wait(tk)
+            torch.cuda.synchronize()
+            assert torch.equal(out, alone[s]), s
+    finally:
+        server.close()
+        v.close()
+
+
 def test_requests_queued_behind_a_busy_slot_are_fused(cuda, rpl_lib):
     """With one stream slot, requests submitted while a long request occupies it wait in the queue
     and go out together in the next launch, each still equal to its render alone."""
