@@ -592,11 +592,11 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 
 // Slab tests of the two child boxes of a binary node (n0: child 0's x and y lo/hi, n1: child 1's, n2:
 // both z lo/hi) against (0, tmax]: the (lo, hi) plane distances of each axis come from one packed fma
-// on the adjacent pair, the same arithmetic as slab().  Returns the entry distances, or +inf for a
-// child the ray misses.
+// on the adjacent pair, the same arithmetic as slab().  Returns the entry distances and whether the
+// ray meets each child within (0, tmax].
 __device__ __forceinline__ void slab_pair(const float2 &ix, const float2 &iy, const float2 &iz, const float2 &ox,
                                           const float2 &oy, const float2 &oz, const float4 &n0, const float4 &n1,
-                                          const float4 &n2, float tmax, float &t0, float &t1) {
+                                          const float4 &n2, float tmax, float &t0, float &t1, bool &h0, bool &h1) {
     const float2 x0 = fma2(make_float2(n0.x, n0.y), ix, ox), y0 = fma2(make_float2(n0.z, n0.w), iy, oy);
     const float2 z0 = fma2(make_float2(n2.x, n2.y), iz, oz);
     const float2 x1 = fma2(make_float2(n1.x, n1.y), ix, ox), y1 = fma2(make_float2(n1.z, n1.w), iy, oy);
@@ -605,8 +605,10 @@ __device__ __forceinline__ void slab_pair(const float2 &ix, const float2 &iy, co
     const float out0 = fminf(fminf(fmaxf(x0.x, x0.y), fmaxf(y0.x, y0.y)), fminf(fmaxf(z0.x, z0.y), tmax));
     const float in1 = fmaxf(fmaxf(fminf(x1.x, x1.y), fminf(y1.x, y1.y)), fmaxf(fminf(z1.x, z1.y), 0.0f));
     const float out1 = fminf(fminf(fmaxf(x1.x, x1.y), fmaxf(y1.x, y1.y)), fminf(fmaxf(z1.x, z1.y), tmax));
-    t0 = in0 <= out0 ? in0 : CUDART_INF_F;
-    t1 = in1 <= out1 ? in1 : CUDART_INF_F;
+    t0 = in0;
+    t1 = in1;
+    h0 = in0 <= out0;
+    h1 = in1 <= out1;
 }
 
 // Vertex relative to the ray origin, permuted so the dominant axis comes last, then sheared so that
@@ -760,10 +762,10 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
             const int4 n3 = __ldg(reinterpret_cast<const int4 *>(n + 3));
             if (kCount) ++cnt.nodes;
             float t0, t1;
-            slab_pair(ix, iy, iz, ox, oy, oz, n0, n1, n2, tmax, t0, t1);
+            bool h0, h1;
+            slab_pair(ix, iy, iz, ox, oy, oz, n0, n1, n2, tmax, t0, t1, h0, h1);
             // leaf children arrive encoded and empty ones never hit (device layout, see rpl_api.cpp)
             const int e0 = n3.x, e1 = n3.y;
-            const bool h0 = t0 != CUDART_INF_F, h1 = t1 != CUDART_INF_F;
             // nearer hit child next (child 0 on a tie), the other one pushed; branch-free selects
             const bool sw = h1 && (!h0 || t1 < t0);
             const int near = sw ? e1 : e0, far = sw ? e0 : e1;
