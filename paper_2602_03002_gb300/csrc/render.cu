@@ -590,6 +590,19 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
     return d;
 }
 
+// Three-input minimum and maximum (min.f32 / max.f32 with three sources, sm_100 and later): the same
+// value as two nested fminf / fmaxf, in one instruction.
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // Slab tests of the two child boxes of a binary node (n0: child 0's x and y lo/hi, n1: child 1's, n2:
 // both z lo/hi) against (0, tmax]: the (lo, hi) plane distances of each axis come from one packed fma
 // on the adjacent pair, the same arithmetic as slab().  Returns the entry distances and whether the
@@ -601,10 +614,10 @@ __device__ __forceinline__ void slab_pair(const float2 &ix, const float2 &iy, co
     const float2 z0 = fma2(make_float2(n2.x, n2.y), iz, oz);
     const float2 x1 = fma2(make_float2(n1.x, n1.y), ix, ox), y1 = fma2(make_float2(n1.z, n1.w), iy, oy);
     const float2 z1 = fma2(make_float2(n2.z, n2.w), iz, oz);
-    const float in0 = fmaxf(fmaxf(fminf(x0.x, x0.y), fminf(y0.x, y0.y)), fmaxf(fminf(z0.x, z0.y), 0.0f));
-    const float out0 = fminf(fminf(fmaxf(x0.x, x0.y), fmaxf(y0.x, y0.y)), fminf(fmaxf(z0.x, z0.y), tmax));
-    const float in1 = fmaxf(fmaxf(fminf(x1.x, x1.y), fminf(y1.x, y1.y)), fmaxf(fminf(z1.x, z1.y), 0.0f));
-    const float out1 = fminf(fminf(fmaxf(x1.x, x1.y), fmaxf(y1.x, y1.y)), fminf(fmaxf(z1.x, z1.y), tmax));
+    const float in0 = fmax3(fminf(x0.x, x0.y), fminf(y0.x, y0.y), fmaxf(fminf(z0.x, z0.y), 0.0f));
+    const float out0 = fmin3(fmaxf(x0.x, x0.y), fmaxf(y0.x, y0.y), fminf(fmaxf(z0.x, z0.y), tmax));
+    const float in1 = fmax3(fminf(x1.x, x1.y), fminf(y1.x, y1.y), fmaxf(fminf(z1.x, z1.y), 0.0f));
+    const float out1 = fmin3(fmaxf(x1.x, x1.y), fmaxf(y1.x, y1.y), fminf(fmaxf(z1.x, z1.y), tmax));
     t0 = in0;
     t1 = in1;
     h0 = in0 <= out0;
@@ -633,8 +646,8 @@ __device__ __forceinline__ float3 shear_vertex(const Ray &r, float vx, float vy,
 // distance.  The arithmetic is spelled out with round-to-nearest intrinsics, so every caller gets
 // the same bits for the same inputs.
 __device__ __forceinline__ bool tri_finish(float U, float V, float W, float az, float bz, float cz, float &tmax) {
-    const bool has_neg = (U < 0.f) || (V < 0.f) || (W < 0.f);
-    const bool has_pos = (U > 0.f) || (V > 0.f) || (W > 0.f);
+    const bool has_neg = fmin3(U, V, W) < 0.f;
+    const bool has_pos = fmax3(U, V, W) > 0.f;
     if (has_neg && has_pos) return false;
     const float det = __fadd_rn(__fadd_rn(U, V), W);
     if (det == 0.f) return false;
