@@ -120,6 +120,7 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
         d.out_h = k.height;
         d.raw_off = 0;
         d.tiles_x = (k.width + 7) / 8;
+        fastdiv_magic((uint32_t)d.tiles_x, d.tx_m, d.tx_k);
         d.tile_off = tiles;
         d.pix_off = (int32_t)pix;
         d.mount = k.mount_link;
@@ -195,6 +196,7 @@ extern "C" RPL_API rpl_status rpl_render_static_scratch(rpl_scene_t scene, const
             rp.L = n_links;
             rp.C = n_cams;
             rp.tiles_per_env = tiles;
+            if (tiles > 0) fastdiv_magic((uint32_t)tiles, rp.tpe_m, rp.tpe_k);
             rp.pix_per_env = (int32_t)pix;
             rp.depth_kind = sp.depth_kind;
             std::memcpy(rp.lroot, pp.lroot, sizeof(rp.lroot));

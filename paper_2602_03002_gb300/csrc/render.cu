@@ -1145,16 +1145,34 @@ __device__ __forceinline__ void finish_pixel(const RenderParams &p, int e, int c
     }
 }
 
-// Env and tile within the env of tile `warp` (32-bit division whenever the index fits).
-__device__ __forceinline__ void split_tile(int64_t warp, int32_t tiles_per_env, int &e, int &r_tile) {
-    if ((uint64_t)warp < 0x100000000ull) {
-        const uint32_t w = (uint32_t)warp, q = w / (uint32_t)tiles_per_env;
+// floor(n / d) for 0 <= n < 2^31 from the multiplier m and shift k of the divisor d (fastdiv_magic in
+// render.h): one wide multiply and a shift instead of a division.
+__device__ __forceinline__ uint32_t fastdiv(uint32_t n, uint32_t m, uint32_t k) {
+    return (uint32_t)(((uint64_t)n * m) >> k);
+}
+
+// Env and tile within the env of tile `warp`: multiply and shift when the host set the divisor's
+// magic and the index fits in 31 bits, else a 32- or 64-bit division.
+__device__ __forceinline__ void split_tile(int64_t warp, const RenderParams &p, int &e, int &r_tile) {
+    const int32_t tpe = p.tiles_per_env;
+    if ((uint64_t)warp < 0x80000000ull && p.tpe_m != 0u) {
+        const uint32_t q = fastdiv((uint32_t)warp, p.tpe_m, p.tpe_k);
         e = (int)q;
-        r_tile = (int)(w - q * (uint32_t)tiles_per_env);
+        r_tile = (int)((uint32_t)warp - q * (uint32_t)tpe);
+    } else if ((uint64_t)warp < 0x100000000ull) {
+        const uint32_t w = (uint32_t)warp, q = w / (uint32_t)tpe;
+        e = (int)q;
+        r_tile = (int)(w - q * (uint32_t)tpe);
     } else {
-        e = (int)(warp / tiles_per_env);
-        r_tile = (int)(warp - (int64_t)e * tiles_per_env);
+        e = (int)(warp / tpe);
+        r_tile = (int)(warp - (int64_t)e * tpe);
     }
+}
+
+// Row and column of tile t (0 <= t < 2^31) of a camera's tile grid.
+__device__ __forceinline__ void tile_row_col(const CamDev &cam, int t, int &row, int &col) {
+    row = cam.tx_m ? (int)fastdiv((uint32_t)t, cam.tx_m, cam.tx_k) : t / cam.tiles_x;
+    col = t - row * cam.tiles_x;
 }
 
 // Terrain entry node and link mask of a tile, derived by its warp (when no tile-prep output is
@@ -1200,7 +1218,7 @@ __device__ __forceinline__ void tile_reach_in_warp(const RenderParams &p, int e,
 __device__ __forceinline__ int64_t tile_of(const RenderParams &p, int64_t t) {
     if (!p.env_order) return t;
     int e, r;
-    split_tile(t, p.tiles_per_env, e, r);
+    split_tile(t, p, e, r);
     return (int64_t)__ldg(p.env_order + e) * p.tiles_per_env + r;
 }
 
@@ -1208,17 +1226,18 @@ __device__ __forceinline__ int64_t tile_of(const RenderParams &p, int64_t t) {
 // (env, camera).  Called once per warp, or in a grid-stride loop by the persistent launch; `warp` is
 // uniform across the warp so the warp-wide reductions below see all 32 lanes.  kTileInfo: the tile's
 // entry node and link mask come from p.tile_info (else the warp derives them).
+// (e, r_tile: the tile's env and its index inside the env, i.e. warp = e * tiles_per_env + r_tile.)
 template <bool kCount, int kKind, bool kTileInfo>
-__device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp, int lane, int64_t step) {
-    int e, r_tile;
-    split_tile(warp, p.tiles_per_env, e, r_tile);
+__device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp, int e, int r_tile, int lane,
+                                            int64_t step) {
     int c = 0;
     while (c + 1 < p.C && r_tile >= p.cams[c + 1].tile_off) ++c;
     const CamDev &cam = p.cams[c];
-    const int t = r_tile - cam.tile_off;
     const int tw_log2 = p.tile_w_log2, th = 32 >> tw_log2;
-    const int x = (t % cam.tiles_x) * (1 << tw_log2) + (lane & ((1 << tw_log2) - 1));
-    const int y = (t / cam.tiles_x) * th + (lane >> tw_log2);
+    int trow, tcol;
+    tile_row_col(cam, r_tile - cam.tile_off, trow, tcol);
+    const int x = tcol * (1 << tw_log2) + (lane & ((1 << tw_log2) - 1));
+    const int y = trow * th + (lane >> tw_log2);
     // lanes outside a ragged tile still take part in the warp-wide reductions below
     const bool active = x < cam.width && y < cam.height;
     const int xs = min(x, cam.width - 1), ys = min(y, cam.height - 1);
@@ -1339,6 +1358,13 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
     }
 }
 
+template <bool kCount, int kKind, bool kTileInfo>
+__device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp, int lane, int64_t step) {
+    int e, r_tile;
+    split_tile(warp, p, e, r_tile);
+    render_tile<kCount, kKind, kTileInfo>(p, warp, e, r_tile, lane, step);
+}
+
 // kMinBlocks caps registers so that many blocks of 128 threads stay resident per SM (8 -> 64
 // registers, 9 -> 56, 10 -> 48, 12 -> 40).  With p.persistent the grid holds only as many blocks as fit on
 // the device at once and each warp walks the tiles with a grid stride; otherwise one warp per tile.
@@ -1389,14 +1415,32 @@ __device__ __forceinline__ void render_queued(const RenderParams &p, int lane, i
     asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
     int q = (int)(smid % (uint32_t)nq);
     int64_t qsize = queue_size(total, q, nq, chunk), qbegin = queue_begin(total, q, nq);
+    // multiply-and-shift divisions whenever every tile position fits in 31 bits and the host set the
+    // magics of the divisors
+    const bool small = total < 0x7FFFFFFFll && p.tpe_m != 0u && (chunk <= 0 || p.chunk_m != 0u);
 #pragma unroll 1
     for (;;) {
         unsigned long long k = 0ull;
         if (lane == 0) k = atomicAdd(p.queues + q, 1ull);
         k = __shfl_sync(0xffffffffu, k, 0);
         if (k < (unsigned long long)qsize) {
-            render_tile<kCount, kKind, kTileInfo>(p, tile_of(p, queue_tile(q, nq, chunk, qbegin, (int64_t)k)), lane,
-                                                  step);
+            // the tile's position in processing order, then its env (through the env order) and index
+            int e, r;
+            if (small) {
+                uint32_t pos;
+                if (chunk <= 0) {
+                    pos = (uint32_t)(qbegin + (int64_t)k);
+                } else {
+                    const uint32_t j = fastdiv((uint32_t)k, p.chunk_m, p.chunk_k);
+                    pos = (uint32_t)(q + j * nq) * (uint32_t)chunk + ((uint32_t)k - j * (uint32_t)chunk);
+                }
+                e = (int)fastdiv(pos, p.tpe_m, p.tpe_k);
+                r = (int)(pos - (uint32_t)e * (uint32_t)p.tiles_per_env);
+            } else {
+                split_tile(queue_tile(q, nq, chunk, qbegin, (int64_t)k), p, e, r);
+            }
+            if (p.env_order) e = __ldg(p.env_order + e);
+            render_tile<kCount, kKind, kTileInfo>(p, (int64_t)e * p.tiles_per_env + r, e, r, lane, step);
             continue;
         }
         // this queue is empty: the queue with the most tiles left (warp-wide argmax)
@@ -1453,13 +1497,14 @@ __global__ void __launch_bounds__(256, 3) tile_prep_kernel(const __grid_constant
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)p.E * p.tiles_per_env) return;
     int e, r_tile;
-    split_tile(i, p.tiles_per_env, e, r_tile);
+    split_tile(i, p, e, r_tile);
     int c = 0;
     while (c + 1 < p.C && r_tile >= p.cams[c + 1].tile_off) ++c;
     const CamDev &cam = p.cams[c];
-    const int t = r_tile - cam.tile_off;
     const int tw = 1 << p.tile_w_log2, th = 32 >> p.tile_w_log2;
-    const int x0 = (t % cam.tiles_x) * tw, y0 = (t / cam.tiles_x) * th;
+    int trow, tcol;
+    tile_row_col(cam, r_tile - cam.tile_off, trow, tcol);
+    const int x0 = tcol * tw, y0 = trow * th;
     const int x1 = min(x0 + tw, cam.width) - 1, y1 = min(y0 + th, cam.height) - 1;
     float fx = cam.fx, fy = cam.fy, cx = cam.cx, cy = cam.cy;
     if (p.intr) {

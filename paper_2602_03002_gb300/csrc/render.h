@@ -7,12 +7,24 @@
 
 namespace rpl {
 
+// Division by a divisor d (1 <= d < 2^31) for dividends n < 2^31 as a multiply and a shift: with
+// l = ceil(log2 d), k = 31 + l and m = ceil(2^k / d) (which is below 2^32), floor(n / d) = (n m) >> k,
+// since the error term n (m d - 2^k) / (d 2^k) stays below 2^-l <= 1/d (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994).  m = 0 marks an unset divisor.
+inline void fastdiv_magic(uint32_t d, uint32_t &m, uint32_t &k) {
+    uint32_t l = 0;
+    while (l < 31 && (1u << l) < d) ++l;
+    k = 31u + l;
+    m = (uint32_t)(((1ull << k) + d - 1ull) / d);
+}
+
 // One camera as the kernels see it.  width x height is the ray-cast (raw) image, tiled by warps of
 // 32 rays; tile_off is the camera's first tile inside one env.  The output image is out_w x out_h
 // = raw / ds; pix_off is its first pixel inside one env's output, raw_off (ds > 1 only) the first
 // pixel of the raw image inside one env's raw buffer.
 struct CamDev {
     int32_t width, height, tiles_x, tile_off;
+    uint32_t tx_m, tx_k;   // fastdiv_magic of tiles_x (0 = unset)
     int32_t ds, out_w, out_h, raw_off;
     int32_t pix_off, mount;
     float fx, fy, cx, cy, d_min, d_max;
@@ -97,6 +109,7 @@ struct RenderParams {
     int4 *tile_info;
     const float *intr;      // [E, C, 4] per-env (fx, fy, cx, cy) or null
     int32_t E, L, C, tiles_per_env;
+    uint32_t tpe_m, tpe_k;   // fastdiv_magic of tiles_per_env (0 = unset)
     int32_t pix_per_env, depth_kind;
     int32_t lroot[RPL_MAX_LINKS];   // root node of each link BVH in lnodes, -1 = no mesh
     CamDev cams[RPL_MAX_CAMERAS];
@@ -124,6 +137,7 @@ struct RenderParams {
     // or dealt to them in chunks of the tiles of chunk_envs envs; null otherwise
     unsigned long long *queues;
     int32_t n_queues, chunk_envs;
+    uint32_t chunk_m, chunk_k;   // fastdiv_magic of chunk_envs * tiles_per_env (0 = unset)
     // processing order of the envs ([E] env indices, sorted by position), or null for index order
     const int32_t *env_order;
     // fused launches only (render_multi_kernel): tiles of this request still running, and a word in

@@ -845,6 +845,7 @@ static int32_t fill_cams(const rpl_view *v, CamDev *out) {
         d.width = k.width;
         d.height = k.height;
         d.tiles_x = (k.width + tw - 1) / tw;
+        fastdiv_magic((uint32_t)d.tiles_x, d.tx_m, d.tx_k);
         d.tile_off = toff;
         toff += d.tiles_x * ((k.height + th - 1) / th);
         d.ds = k.downsample <= 1 ? 1 : k.downsample;
@@ -949,6 +950,7 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
     rp.L = v->L;
     rp.C = v->C;
     rp.tiles_per_env = tiles_per_env;
+    if (tiles_per_env > 0) fastdiv_magic((uint32_t)tiles_per_env, rp.tpe_m, rp.tpe_k);
     rp.tile_w_log2 = v->tune.tile_w_log2;
     rp.persistent = v->tune.persistent;
     rp.terrain_first = v->tune.terrain_first;
@@ -982,6 +984,8 @@ static rpl_status build_params(rpl_view *v, const float *poses_dev, int64_t step
     rp.queues = pp.queues;
     rp.n_queues = pp.n_queues;
     rp.chunk_envs = v->tune.chunk_envs;
+    const int64_t chunk = (int64_t)rp.chunk_envs * tiles_per_env;
+    if (chunk > 0 && chunk < 0x7FFFFFFFll) fastdiv_magic((uint32_t)chunk, rp.chunk_m, rp.chunk_k);
     rp.env_order = v->tune.env_order ? v->env_order.as<const int32_t>() : nullptr;
     return RPL_OK;
 }
