@@ -708,10 +708,12 @@ __device__ __forceinline__ void leaf(const float4 *__restrict__ tris, int first,
 #endif
     int i = first;
     if (count == 2) {
+        // the second triangle's last vertex is loaded with the first triangle, so that a quad's four
+        // vertices arrive together instead of after the quad flag in b.w
         const float4 a = __ldg(tris + 3 * i), b = __ldg(tris + 3 * i + 1), c = __ldg(tris + 3 * i + 2);
+        const float4 d = __ldg(tris + 3 * i + 5);
         if (b.w != 0.f) {
-            // a quad: the second triangle is (a, c, d); only its last vertex is loaded
-            const float4 d = __ldg(tris + 3 * i + 5);
+            // a quad: the second triangle is (a, c, d)
             if (kCount) cnt.tris += 2;
             hit |= quad_hit<kSplit>(r, a, b, c, d, tmax);
             return;
