@@ -2,12 +2,15 @@
 // the depth-sensor model (Appendix A.2).
 //
 //   prep_kernel    one thread per (env, link): normalised link rotation, world->link transform and
-//                  the link's world AABB; one thread per (env, camera): camera pose = link pose
-//                  composed with the (optionally per-env randomised) mount offset.
+//                  the link's world AABB; four threads per (env, camera): camera pose = link pose
+//                  composed with the (optionally per-env randomised) mount offset, the links in the
+//                  camera's view volume, its terrain entry node and latency word.
+//   tile_prep_kernel  one thread per 32-pixel tile: terrain entry subtrees and link mask of the tile.
 //   render_kernel  one thread per pixel ray, one warp per 32-pixel tile of one (env, camera):
-//                  BuildDepthRay -> links whose world AABB the ray meets within the running bound
-//                  (ray moved into the link frame, link BVH traversed, bound shrinks on each hit)
-//                  -> terrain BVH traversal with the bound -> far-plane clip -> fused sensor model
+//                  BuildDepthRay -> terrain BVH traversal -> links whose world AABB the ray meets
+//                  within the running bound (ray moved into the link frame, link BVH traversed,
+//                  bound shrinks on each hit; the order of the two queries is a launch-shape
+//                  option) -> far-plane clip -> fused sensor model
 //                  (ring-buffer write, latency select, noise, clip, dropout, side mask) -> store;
 //                  rays of a downsampled camera store their raw depth instead.
 //   downsample_kernel  one thread per output pixel of a downsampled camera: mean of its raw block
@@ -445,7 +448,13 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
         p.link_box[2 * i + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
         return;
     }
-    const int64_t j = i - n_link;
+    // four consecutive threads per (env, camera), from the first warp boundary after the link threads
+    // on: each tests a quarter of the links against the view volume, so that the camera's chain of
+    // work is a quarter as long
+    const int64_t cam0 = (n_link + 31) & ~(int64_t)31;
+    if (i < cam0) return;
+    const int64_t j = (i - cam0) >> 2;
+    const int sub = (int)((i - cam0) & 3);
     if (j >= (int64_t)p.E * p.C) return;
     const int e = (int)(j / p.C), c = (int)(j % p.C);
     const CamDev &cam = p.cams[c];
@@ -479,10 +488,12 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
     const float ox = Rl[0] * op[0] + Rl[1] * op[1] + Rl[2] * op[2];
     const float oy = Rl[3] * op[0] + Rl[4] * op[1] + Rl[5] * op[2];
     const float oz = Rl[6] * op[0] + Rl[7] * op[1] + Rl[8] * op[2];
-    p.cam_xf[5 * j + 0] = make_float4(Rc[0], Rc[1], Rc[2], q[0]);
-    p.cam_xf[5 * j + 1] = make_float4(Rc[3], Rc[4], Rc[5], q[1]);
-    p.cam_xf[5 * j + 2] = make_float4(Rc[6], Rc[7], Rc[8], q[2]);
-    p.cam_xf[5 * j + 3] = make_float4(ox, oy, oz, 0.f);
+    if (sub == 0) {
+        p.cam_xf[5 * j + 0] = make_float4(Rc[0], Rc[1], Rc[2], q[0]);
+        p.cam_xf[5 * j + 1] = make_float4(Rc[3], Rc[4], Rc[5], q[1]);
+        p.cam_xf[5 * j + 2] = make_float4(Rc[6], Rc[7], Rc[8], q[2]);
+        p.cam_xf[5 * j + 3] = make_float4(ox, oy, oz, 0.f);
+    }
 
     // The camera's view volume: apex o, far face at z-depth d_max through the four corner pixels.
     // Every pixel ray segment of this camera (z-depth or range) lies inside it.
@@ -505,9 +516,10 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
     const float axis[3] = {Rc[2], Rc[5], Rc[8]};
     make_pyramid(V, o, B, axis, cam.d_max);
 
-    // 1) links whose world AABB meets the view pyramid
+    // 1) links whose world AABB meets the view pyramid: links sub, sub + 4, ... by each of the four
+    //    threads, the masks OR-ed across them (the four are consecutive lanes of one warp)
     uint64_t mask = 0;
-    for (int l = 0; l < p.L; ++l) {
+    for (int l = sub; l < p.L; l += 4) {
         if (p.lroot[l] < 0) continue;
         const int64_t el = (int64_t)e * p.L + l;
         const float *ql = p.poses + 7 * el;
@@ -516,6 +528,12 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepP
         if (!link_world_box(p, el, l, R, lo, hi)) continue;
         if (pyramid_meets_box(V, lo, hi)) mask |= 1ull << l;
     }
+    {
+        const unsigned group = 0xFu << (threadIdx.x & 28);
+        mask |= __shfl_xor_sync(group, mask, 1);
+        mask |= __shfl_xor_sync(group, mask, 2);
+    }
+    if (sub != 0) return;
 
     // 2) terrain entry node: descend while exactly one child's box meets the view volume's AABB and
     //    that child is an inner node; nothing in the other subtrees can be hit by this camera's rays
@@ -1714,8 +1732,9 @@ __global__ void __launch_bounds__(1024) env_order_kernel(const uint32_t *__restr
 }  // namespace
 
 cudaError_t launch_prep(const PrepParams &p, cudaStream_t s) {
-    const int64_t n = (int64_t)p.E * (p.L + p.C);
-    if (n == 0) return cudaSuccess;
+    if ((int64_t)p.E * (p.L + p.C) == 0) return cudaSuccess;
+    // one thread per (env, link), then (from a warp boundary) four per (env, camera)
+    const int64_t n = (((int64_t)p.E * p.L + 31) & ~(int64_t)31) + 4 * (int64_t)p.E * p.C;
     (void)cudaGetLastError();   // report only this launch's error, not a stale one
     prep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p);
     return cudaGetLastError();

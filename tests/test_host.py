@@ -69,6 +69,61 @@ int main(void) {
     assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
 
 
+def test_tile_index_division_magic_is_exact(tmp_path):
+    """The kernels split tile indices by a multiply and a shift with the multiplier and shift the host
+    computes per launch (fastdiv_magic in render.h).  Exact division is the reference: every divisor
+    1..4096, powers of two and their neighbours up to 2^31 - 1, and pseudo-random divisors, each on
+    dividends at the ends of [0, 2^31) and around multiples of the divisor."""
+    import shutil
+    import subprocess
+    if shutil.which("g++") is None:
+        pytest.skip("no C++ compiler")
+    src = tmp_path / "fastdiv.cpp"
+    src.write_text(r"""
+#include <cstdint>
+#include <cstdio>
+#include "render.h"
+static uint32_t qdiv(uint32_t n, uint32_t m, uint32_t k) { return (uint32_t)(((uint64_t)n * m) >> k); }
+static int check(uint32_t d) {
+    uint32_t m = 0, k = 0;
+    rpl::fastdiv_magic(d, m, k);
+    if (m == 0) return 1;
+    const uint32_t top = 0x7FFFFFFFu;
+    const uint32_t ns[] = {0u, 1u, d - 1u, d, d + 1u, 2u * d - 1u, top, top - 1u, top / d * d, top / d * d - 1u,
+                           (top / d / 2u) * d, (top / d / 2u) * d - 1u, 123456789u % (top + 1u)};
+    for (uint32_t n : ns)
+        if (n <= top && qdiv(n, m, k) != n / d) { std::printf("d=%u n=%u\n", d, n); return 2; }
+    for (uint32_t n = 0; n < 20000u && (uint64_t)n < 3ull * d + 5u; ++n)
+        if (qdiv(n, m, k) != n / d) { std::printf("d=%u n=%u\n", d, n); return 3; }
+    return 0;
+}
+int main() {
+    for (uint32_t d = 1; d <= 4096; ++d) if (int r = check(d)) return r;
+    for (int b = 12; b < 31; ++b)
+        for (int o = -2; o <= 2; ++o) if (int r = check((1u << b) + (uint32_t)o)) return r;
+    if (int r = check(0x7FFFFFFFu)) return r;
+    uint64_t x = 88172645463325252ull;
+    for (int i = 0; i < 2000; ++i) {
+        x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+        const uint32_t d = (uint32_t)(x % 0x7FFFFFFFull) + 1u;
+        if (int r = check(d)) return r;
+    }
+    std::printf("ok\n");
+    return 0;
+}
+""")
+    exe = tmp_path / "fastdiv"
+    csrc = os.path.join(ROOT, "paper_2602_03002_gb300", "csrc")
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    r = subprocess.run(["g++", "-std=c++17", "-O1", "-I", csrc, "-I", os.path.join(ROOT, "include"), "-I", cuda_inc,
+                        str(src), "-o", str(exe)], capture_output=True, text=True)
+    if r.returncode != 0 and "cuda_runtime.h" in r.stderr:
+        pytest.skip("CUDA headers not found")
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout)
+
+
 def test_scene_create_fails_cleanly_without_gpu(rpl_lib):
     import torch
     if torch.cuda.is_available():
