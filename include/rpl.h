@@ -277,7 +277,7 @@ RPL_API rpl_status rpl_view_host_async(rpl_view_t view, int32_t enable);
  * the bodies first; the depth is the same either way); min_blocks: 8 (up to 64 registers per
  * thread), 9 (up to 56), 10 (up to 48) or 12 (up to 40) resident blocks of 128 threads per SM.  The
  * shape never changes the result, only the speed.  Default: 4x8, persistent 2 (per-SM queues), links
- * first, 9, env_order 1, chunk_envs 1. */
+ * first, 8, env_order 1, chunk_envs 1. */
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t persistent;

@@ -1385,6 +1385,132 @@ __device__ __forceinline__ void render_tile(const RenderParams &p, int64_t warp,
     render_tile<kCount, kKind, kTileInfo>(p, warp, e, r_tile, lane, step);
 }
 
+// What a tile's rays need, derived from (env, tile within the env, lane): camera, pixel, ray,
+// z-depth scale, initial bound, latency word, terrain entry nodes and link mask.  The same arithmetic
+// as render_tile's setup, so the rays are bit-identical.
+struct TileSetup {
+    int c, x, y;
+    bool active;
+    float3 d, base, off;
+    float m, tmax0;
+    uint32_t lat;
+    int entry, entry2;
+    uint64_t link_mask;
+};
+
+__device__ __forceinline__ TileSetup tile_setup(const RenderParams &p, int64_t warp, int e, int r_tile, int lane) {
+    TileSetup t;
+    int c = 0;
+    while (c + 1 < p.C && r_tile >= p.cams[c + 1].tile_off) ++c;
+    const CamDev &cam = p.cams[c];
+    const int tw_log2 = p.tile_w_log2, th = 32 >> tw_log2;
+    int trow, tcol;
+    tile_row_col(cam, r_tile - cam.tile_off, trow, tcol);
+    t.c = c;
+    t.x = tcol * (1 << tw_log2) + (lane & ((1 << tw_log2) - 1));
+    t.y = trow * th + (lane >> tw_log2);
+    t.active = t.x < cam.width && t.y < cam.height;
+    const int xs = min(t.x, cam.width - 1), ys = min(t.y, cam.height - 1);
+    float fx = cam.fx, fy = cam.fy, cx = cam.cx, cy = cam.cy;
+    if (p.intr) {
+        const float4 k = __ldg(reinterpret_cast<const float4 *>(p.intr) + (int64_t)e * p.C + c);
+        fx = k.x; fy = k.y; cx = k.z; cy = k.w;
+    }
+    const float4 *cx4 = p.cam_xf + 5 * ((int64_t)e * p.C + c);
+    const float4 R0 = __ldg(cx4), R1 = __ldg(cx4 + 1), R2 = __ldg(cx4 + 2), OF = __ldg(cx4 + 3);
+    const float4 CV = __ldg(cx4 + 4);
+    const float rx = __fdividef((float)xs - cx, fx), ry = __fdividef((float)ys - cy, fy);
+    const float inv_n = rsqrtf(rx * rx + ry * ry + 1.0f);
+    const float ux = rx * inv_n, uy = ry * inv_n, uz = inv_n;
+    t.d = make_float3(R0.x * ux + R0.y * uy + R0.z * uz, R1.x * ux + R1.y * uy + R1.z * uz,
+                      R2.x * ux + R2.y * uy + R2.z * uz);
+    t.base = make_float3(R0.w, R1.w, R2.w);
+    t.off = make_float3(OF.x, OF.y, OF.z);
+    t.m = p.depth_kind == RPL_DEPTH_Z ? inv_n : 1.0f;
+    t.tmax0 = __fdividef(cam.d_max, t.m);
+    t.lat = __float_as_uint(CV.w);
+    const int4 ti = __ldg(p.tile_info + warp);
+    t.entry = ti.x;
+    t.entry2 = ti.w;
+    t.link_mask = ((uint64_t)(uint32_t)ti.z << 32) | (uint32_t)ti.y;
+    return t;
+}
+
+// One tile with tile info, links queried first (Alg. 1's order), in the per-SM queued launch: the
+// same results as render_tile, but for a tile with links to test the setup is derived again after
+// the link queries (the compiler is kept from reusing it) instead of being held in registers
+// through them, which lowers the register pressure of the whole kernel (the terrain traversal runs
+// with fewer spills).
+template <int kKind>
+__device__ __forceinline__ void render_tile_links_first(const RenderParams &p, int64_t warp, int e, int r_tile,
+                                                        int lane, int64_t step) {
+    TileSetup t = tile_setup(p, warp, e, r_tile, lane);
+    if (!t.active) return;
+    float tmax = t.tmax0;
+    bool hit = false, ok = true;
+    Counts cnt;
+#ifdef RPL_CHECKED
+    uint32_t ck_err = 0;
+#endif
+    if (t.link_mask != 0) {
+        // 1) the robot bodies the tile can reach: rays move into each link frame
+        Ray ray;
+        make_ray(ray, t.base, t.off, t.d);
+        const float3 base = t.base, off = t.off, d = t.d;
+        const uint64_t link_mask = t.link_mask;
+#pragma unroll 1
+        for (uint64_t mk = link_mask; mk; mk &= mk - 1) {
+            const int l = __ffsll((long long)mk) - 1;
+            const int root = p.lroot[l];
+            if (root < 0) continue;
+            const int64_t el = (int64_t)e * p.L + l;
+            const float4 blo = __ldg(p.link_box + 2 * el), bhi = __ldg(p.link_box + 2 * el + 1);
+            if (slab(ray, blo.x, bhi.x, blo.y, bhi.y, blo.z, bhi.z, tmax) == CUDART_INF_F) continue;
+            const float4 X0 = __ldg(p.link_xf + 3 * el), X1 = __ldg(p.link_xf + 3 * el + 1),
+                         X2 = __ldg(p.link_xf + 3 * el + 2);
+            const float3 rel = make_float3((base.x - X0.w) + off.x, (base.y - X1.w) + off.y, (base.z - X2.w) + off.z);
+            const float3 ob = make_float3(X0.x * rel.x + X0.y * rel.y + X0.z * rel.z,
+                                          X1.x * rel.x + X1.y * rel.y + X1.z * rel.z,
+                                          X2.x * rel.x + X2.y * rel.y + X2.z * rel.z);
+            const float3 db = make_float3(X0.x * d.x + X0.y * d.y + X0.z * d.z, X1.x * d.x + X1.y * d.y + X1.z * d.z,
+                                          X2.x * d.x + X2.y * d.y + X2.z * d.z);
+            Ray lr;
+            make_ray(lr, ob, make_float3(0.f, 0.f, 0.f), db);
+            ok &= traverse<false, false>(p.lnodes, p.ltris, root, -1, lr, tmax, hit, cnt
+                                         RPL_CK_ARGS(p.n_lnodes, p.n_ltris, ck_err));
+        }
+        // an empty asm that may change these inputs, as far as the compiler knows: the setup is
+        // computed again from them rather than kept live through the link queries
+        asm volatile("" : "+r"(r_tile), "+l"(warp), "+r"(e));
+        t = tile_setup(p, warp, e, r_tile, lane);
+    }
+    // 2) the static terrain, bounded by the closest body hit
+    Ray ray;
+    make_ray(ray, t.base, t.off, t.d);
+    if (kKind == RPL_BVH8Q8) {
+        const int oct = (t.d.x < 0.f ? 1 : 0) | (t.d.y < 0.f ? 2 : 0) | (t.d.z < 0.f ? 4 : 0);
+        ok &= traverse8<false>(p.tnodes, p.ttris, t.entry, ray, oct, tmax, hit, cnt
+                               RPL_CK_ARGS(p.n_tnodes, p.n_ttris, ck_err));
+    } else if (kKind == RPL_BVH4) {
+        ok &= traverse4<false>(p.tnodes, p.ttris, t.entry, ray, tmax, hit, cnt RPL_CK_ARGS(p.n_tnodes, p.n_ttris, ck_err));
+    } else {
+        ok &= traverse<true, false>(p.tnodes, p.ttris, t.entry, t.entry2, ray, tmax, hit, cnt
+                                    RPL_CK_ARGS(p.n_tnodes, p.n_ttris, ck_err));
+    }
+    if (!ok) atomicOr(p.err, 1);
+#ifdef RPL_CHECKED
+    if (ck_err) atomicOr(p.err, (int)ck_err);
+#endif
+    const CamDev &cam = p.cams[t.c];
+    const float z = hit ? fminf(t.m * tmax, cam.d_max) : cam.d_max;
+    if (cam.ds > 1) {
+        // downsampled camera: keep the raw depth; downsample_kernel averages and finishes it
+        p.raw[(int64_t)e * p.raw_per_env + cam.raw_off + (int64_t)t.y * cam.width + t.x] = z;
+    } else {
+        finish_pixel(p, e, t.c, cam, t.x, t.y, z, step, t.lat);
+    }
+}
+
 // kMinBlocks caps registers so that many blocks of 128 threads stay resident per SM (8 -> 64
 // registers, 9 -> 56, 10 -> 48, 12 -> 40).  With p.persistent the grid holds only as many blocks as fit on
 // the device at once and each warp walks the tiles with a grid stride; otherwise one warp per tile.
@@ -1427,7 +1553,8 @@ __device__ __forceinline__ int64_t queue_tile(int q, int nq, int64_t chunk, int6
 // empty the warp moves to the queue with the most tiles left, until every queue is empty.  Each
 // warp that finds its queue empty reads every counter (bypassing L1), so it ends only when all
 // queues were seen empty.
-template <bool kCount, int kKind, bool kTileInfo>
+// kLinksFirst (with tile info, not counting): the tiles are rendered by render_tile_links_first.
+template <bool kCount, int kKind, bool kTileInfo, bool kLinksFirst = false>
 __device__ __forceinline__ void render_queued(const RenderParams &p, int lane, int64_t total, int64_t step) {
     const int nq = p.n_queues;
     const int64_t chunk = (int64_t)p.chunk_envs * p.tiles_per_env;
@@ -1460,7 +1587,10 @@ __device__ __forceinline__ void render_queued(const RenderParams &p, int lane, i
                 split_tile(queue_tile(q, nq, chunk, qbegin, (int64_t)k), p, e, r);
             }
             if (p.env_order) e = __ldg(p.env_order + e);
-            render_tile<kCount, kKind, kTileInfo>(p, (int64_t)e * p.tiles_per_env + r, e, r, lane, step);
+            if constexpr (kLinksFirst && kTileInfo && !kCount)
+                render_tile_links_first<kKind>(p, (int64_t)e * p.tiles_per_env + r, e, r, lane, step);
+            else
+                render_tile<kCount, kKind, kTileInfo>(p, (int64_t)e * p.tiles_per_env + r, e, r, lane, step);
             continue;
         }
         // this queue is empty: the queue with the most tiles left (warp-wide argmax)
@@ -1491,13 +1621,13 @@ __device__ __forceinline__ void render_queued(const RenderParams &p, int lane, i
     }
 }
 
-template <bool kCount, int kKind, int kMinBlocks, bool kTileInfo = true, bool kQueued = false>
+template <bool kCount, int kKind, int kMinBlocks, bool kTileInfo = true, bool kQueued = false, bool kLinksFirst = false>
 __global__ void __launch_bounds__(128, kMinBlocks) render_kernel(const __grid_constant__ RenderParams p) {
     const int lane = threadIdx.x & 31;
     const int64_t total = (int64_t)p.E * p.tiles_per_env;
     const int64_t step = p.step_dev ? *p.step_dev : p.step;
     if (kQueued) {
-        render_queued<kCount, kKind, kTileInfo>(p, lane, total, step);
+        render_queued<kCount, kKind, kTileInfo, kLinksFirst>(p, lane, total, step);
         return;
     }
     const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -1749,6 +1879,14 @@ void launch_kind(const RenderParams &p, bool count, int min_blocks, unsigned g, 
         render_kernel<false, kKind, 8, false><<<g, 128, 0, s>>>(p);   // callers without tile prep (no counters)
     else if (count)
         render_kernel<true, kKind, 8><<<g, 128, 0, s>>>(p);
+    else if (p.queues && !p.terrain_first && min_blocks == 12)
+        render_kernel<false, kKind, 12, true, true, true><<<g, 128, 0, s>>>(p);
+    else if (p.queues && !p.terrain_first && min_blocks == 10)
+        render_kernel<false, kKind, 10, true, true, true><<<g, 128, 0, s>>>(p);
+    else if (p.queues && !p.terrain_first && min_blocks == 9)
+        render_kernel<false, kKind, 9, true, true, true><<<g, 128, 0, s>>>(p);
+    else if (p.queues && !p.terrain_first)
+        render_kernel<false, kKind, 8, true, true, true><<<g, 128, 0, s>>>(p);
     else if (p.queues && min_blocks == 12)
         render_kernel<false, kKind, 12, true, true><<<g, 128, 0, s>>>(p);
     else if (p.queues && min_blocks == 10)

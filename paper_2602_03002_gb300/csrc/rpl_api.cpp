@@ -293,9 +293,9 @@ struct rpl_view {
     cudaEvent_t ev[2 * kTimingSlots] = {};
     int64_t n_timed = 0;
     // launch shape of the render kernel: 4x8 tiles, per-SM tile queues dealt one env at a time in the
-    // spatial order of the envs, links first, 9 blocks per SM (the fastest shape of the autotuner's
+    // spatial order of the envs, links first, 8 blocks per SM (the fastest shape of the autotuner's
     // sweep on the 4096-env scale workload)
-    Tuning tune{2, 2, 0, 9, 1, 1};
+    Tuning tune{2, 2, 0, 8, 1, 1};
     // graph replay (rpl_render_graph): device step counter, captured graph and what it was captured for
     DevBuf d_step;
     int64_t dev_step_next = INT64_MIN; // value the device counter holds before the next replay

@@ -371,7 +371,7 @@ def rpl_static_scratch_status(scene: int, stream=None):
 
 
 def rpl_view_tuning_set(view: int, tile_w: int = 4, tile_h: int = 8, persistent: int = 2, terrain_first: int = 0,
-                        min_blocks: int = 9, env_order: int = 1, chunk_envs: int = 1):
+                        min_blocks: int = 8, env_order: int = 1, chunk_envs: int = 1):
     t = rpl_tuning(tile_w, tile_h, persistent, terrain_first, min_blocks, env_order, chunk_envs)
     _check(lib().rpl_view_tuning_set(view, ctypes.byref(t)))
 
