@@ -7,10 +7,11 @@
 //                  camera's view volume, its terrain entry node and latency word.
 //   tile_prep_kernel  one thread per 32-pixel tile: terrain entry subtrees and link mask of the tile.
 //   render_kernel  one thread per pixel ray, one warp per 32-pixel tile of one (env, camera):
-//                  BuildDepthRay -> terrain BVH traversal -> links whose world AABB the ray meets
-//                  within the running bound (ray moved into the link frame, link BVH traversed,
-//                  bound shrinks on each hit; the order of the two queries is a launch-shape
-//                  option) -> far-plane clip -> fused sensor model
+//                  BuildDepthRay -> links whose world AABB the ray meets within the running bound
+//                  (ray moved into the link frame, link BVH traversed, bound shrinks on each hit)
+//                  -> terrain BVH traversal with the bound (the order of the two queries is a
+//                  launch-shape option; links first, Alg. 1's order, by default) -> far-plane clip
+//                  -> fused sensor model
 //                  (ring-buffer write, latency select, noise, clip, dropout, side mask) -> store;
 //                  rays of a downsampled camera store their raw depth instead.
 //   downsample_kernel  one thread per output pixel of a downsampled camera: mean of its raw block
